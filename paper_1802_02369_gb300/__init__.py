@@ -1,0 +1,7 @@
+"""GB300-native fused collide-stream step of the coupled D1Q3Q3 entropy lattice Boltzmann scheme
+(Dubois, Graille, Lallemand, sections 6 and 8).
+
+Importing the package loads nothing compiled; ``paper_1802_02369_gb300.lbm`` loads the CUDA
+library ``liblbm.so`` on first use and raises if it is missing.
+"""
+__all__ = ["lbm", "workloads"]

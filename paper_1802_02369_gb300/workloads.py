@@ -1,0 +1,122 @@
+"""Seeded synthetic initial data shaped like the experiments of section 9 (periodic acoustic
+waves of growing amplitude) and the Riemann problems used to exercise shocks.
+
+This module holds no arithmetic of the lattice Boltzmann method: it only produces the
+macroscopic fields (rho, u, p) and per-lattice parameters that both the CUDA library and the CPU
+oracle take as inputs. Every generator is deterministic in its arguments
+(``numpy.random.default_rng(PCG64(seed))`` where randomness is drawn).
+
+Pressures are given in physical units. ``p_ref`` is the reference pressure the caller uses for
+its equation of state (section 9 takes c0 = lambda/2, so p_ref = rho0 c0^2 / gamma); "adiabatic"
+pressure means the isentrope through (rho0, p_ref): p = p_ref (rho/rho0)^gamma.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def reference_pressure(lam: float = 1.0, gamma: float = 1.4, rho0: float = 1.0) -> float:
+    """p_ref = rho0 c0^2 / gamma with c0 = lambda / 2 (section 9 parameters)."""
+    c0 = lam / 2.0
+    return rho0 * c0 * c0 / gamma
+
+
+def sod(N: int, p_unit: float, rho_l: float = 1.0, p_l: float = 1.0, rho_r: float = 0.5,
+        p_r: float = 0.5):
+    """Riemann data split at N/2: x < N/2 has (rho_l, 0, p_l * p_unit), x >= N/2 has
+    (rho_r, 0, p_r * p_unit)."""
+    j = np.arange(N)
+    left = j < N // 2
+    rho = np.where(left, rho_l, rho_r).astype(np.float64)
+    u = np.zeros(N)
+    p = np.where(left, p_l, p_r) * p_unit
+    return rho, u, p.astype(np.float64)
+
+
+def steepening_wave(N: int, amp: float, p_ref: float, gamma: float = 1.4, rho0: float = 1.0):
+    """One wavelength over the lattice: rho = rho0 (1 + amp sin(2 pi j / N)),
+    u = amp sin(2 pi j / N), adiabatic pressure."""
+    j = np.arange(N, dtype=np.float64)
+    w = np.sin(2.0 * np.pi * j / N)
+    rho = rho0 * (1.0 + amp * w)
+    u = amp * w
+    p = p_ref * (rho / rho0) ** gamma
+    return rho, u, p
+
+
+def progressive_wave(N: int, delta: float, c0: float, p_ref: float, gamma: float = 1.4, rho0: float = 1.0):
+    """Linear progressive acoustic wave of relative amplitude delta (figures 1-3 of section 9):
+    rho = rho0 (1 + delta sin), u = c0 delta sin, adiabatic pressure."""
+    j = np.arange(N, dtype=np.float64)
+    w = np.sin(2.0 * np.pi * j / N)
+    rho = rho0 * (1.0 + delta * w)
+    u = c0 * delta * w
+    p = p_ref * (rho / rho0) ** gamma
+    return rho, u, p
+
+
+def gaussian_bumps(B: int, N: int, seed: int, p_ref: float, amp: float = 0.05, width: float = 64.0,
+                   nbumps: int = 8, gamma: float = 1.4, rho0: float = 1.0):
+    """B periodic lattices of N nodes: rho = rho0 (1 + sum of nbumps Gaussian bumps of amplitude
+    amp * U[0.5, 1] and 1/e half-width width * U[0.5, 1.5] at uniform centres), u = 0,
+    adiabatic pressure. Returns arrays of shape [B, N]."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    j = np.arange(N, dtype=np.float64)
+    rho = np.full((B, N), rho0)
+    for b in range(B):
+        centres = rng.uniform(0, N, nbumps)
+        amps = amp * rng.uniform(0.5, 1.0, nbumps)
+        widths = width * rng.uniform(0.5, 1.5, nbumps)
+        for c, a, w in zip(centres, amps, widths):
+            d = np.abs(j - c)
+            d = np.minimum(d, N - d)
+            rho[b] += rho0 * a * np.exp(-(d / w) ** 2)
+    u = np.zeros((B, N))
+    p = p_ref * (rho / rho0) ** gamma
+    return rho, u, p
+
+
+@dataclass
+class RaggedBatch:
+    """Independent lattices concatenated back to back (CSR layout)."""
+
+    lengths: np.ndarray   # int64 [B]
+    offsets: np.ndarray   # int64 [B + 1]
+    s_e: np.ndarray       # float64 [B], the free relaxation rate of each lattice
+    bc: np.ndarray        # int32 [B], 0 periodic, 1 bounce-back
+    rho: np.ndarray       # float64 [sum lengths]
+    u: np.ndarray
+    p: np.ndarray
+    states: np.ndarray    # float64 [B, 4] = (rho_L, p_L, rho_R, p_R), pressures in units of p_unit
+
+    def lattice(self, b: int):
+        lo, hi = self.offsets[b], self.offsets[b + 1]
+        return self.rho[lo:hi], self.u[lo:hi], self.p[lo:hi]
+
+
+def ragged_batch(B: int, seed: int, p_unit: float, n_min: int = 512, n_max: int = 65536,
+                 s_range=(1.0, 1.9), left=(0.8, 1.2), right=(0.3, 0.7), p_bounce: float = 0.5) -> RaggedBatch:
+    """B Riemann problems of uneven lengths: N_b uniform in [n_min, n_max], s_e uniform in
+    s_range, left state (rho, p) uniform in ``left``, right state uniform in ``right`` (pressures
+    times p_unit), u = 0, split at N_b / 2; boundary periodic or bounce-back with probability
+    p_bounce each."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    lengths = rng.integers(n_min, n_max + 1, B).astype(np.int64)
+    s_e = rng.uniform(s_range[0], s_range[1], B)
+    states = np.stack([rng.uniform(*left, B), rng.uniform(*left, B),
+                       rng.uniform(*right, B), rng.uniform(*right, B)], axis=1)
+    bc = (rng.uniform(0, 1, B) < p_bounce).astype(np.int32)
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    tot = int(offsets[-1])
+    rho = np.empty(tot)
+    u = np.zeros(tot)
+    p = np.empty(tot)
+    for b in range(B):
+        n = int(lengths[b])
+        r, _, pp = sod(n, p_unit, states[b, 0], states[b, 1], states[b, 2], states[b, 3])
+        rho[offsets[b]:offsets[b + 1]] = r
+        p[offsets[b]:offsets[b + 1]] = pp
+    return RaggedBatch(lengths, offsets, s_e, bc, rho, u, p, states)

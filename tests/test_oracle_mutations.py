@@ -1,0 +1,47 @@
+"""The pins must catch plausible mistakes in the oracle: each case plants one mistake in a copy
+of the oracle source (on the CPU), builds it, and requires the pin suite to fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "d1q3q3_oracle.cpp")
+
+MUTANTS = {
+    "e_eq pressure coefficient": ("3.0 * (rho * u * u + p)", "3.0 * (rho * u * u + 0.9 * p)"),
+    "e_eq kinetic term dropped": ("3.0 * (rho * u * u + p)", "3.0 * (p)"),
+    "psi_eq uses J": ("psi_eq = zeta * u;", "psi_eq = rho * u;"),
+    "eps_eq drops e_eq s": ("log(T / T_ref(ph)) + e_eq * s;", "log(T / T_ref(ph));"),
+    "eps_eq drops 1/gamma": ("(2.0 * rho * ph.cp * l2 / ph.gamma)", "(2.0 * rho * ph.cp * l2)"),
+    "gradient missing factor 2": ("const R dudx = (ur - ul) / (2.0 * ph.dx);", "const R dudx = (ur - ul) / (ph.dx);"),
+    "thermal term over T": ("kappa / (T * T) * dTdx * dTdx", "kappa / T * dTdx * dTdx"),
+    "source sign": ("ms[2] = ms[2] + dt * S;", "ms[2] = ms[2] - dt * S;"),
+    "nu drops lambda": ("const R nu = sigma_e * ph.lambda * ph.dx;", "const R nu = sigma_e * ph.dx;"),
+    "psi relaxed with s_e": ("psi + rt.s_psi * (psi_eq - psi)", "psi + rt.s_e * (psi_eq - psi)"),
+    "eps relaxed with s_psi": ("eps + rt.s_eps * (eps_eq - eps)", "eps + rt.s_psi * (eps_eq - eps)"),
+    "M psi row sign": ("{0, 0, 0, 0, c * l, -c * l},", "{0, 0, 0, 0, -c * l, c * l},"),
+    "M eps row weight": ("{0, 0, 0, -2 * c * l * l, c * l * l, c * l * l},", "{0, 0, 0, -c * l * l, c * l * l, c * l * l},"),
+    "EOS exponent": ("exp(ph.gamma * (s - ph.s0) / ph.cp)", "exp((s - ph.s0) / ph.cp)"),
+    "wall ghost velocity": ("if (j == 0) { ul = -u; Tl = T; }", "if (j == 0) { ul = u; Tl = T; }"),
+    "stream wrap swapped": ("else if (ph.bc == 0) { out[1] = fs[1]; out[4] = fs[4]; }",
+                            "else if (ph.bc == 0) { out[2] = fs[1]; out[5] = fs[4]; }"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not found exactly once"
+    mut = tmp_path / "mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    "-o", str(lib), str(mut)], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
