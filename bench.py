@@ -1,0 +1,317 @@
+"""Benchmark of the fused D1Q3Q3 collide-stream step on one lattice of N = 2^26 nodes.
+
+Workload (steepening acoustic wave): rho = 1 + 0.1 sin(2 pi j/N), u = 0.1 sin(2 pi j/N),
+adiabatic pressure, periodic, lambda = 1, free rate s_e = 1.2 with the paper's coupled rates.
+One benchmark "step" is one lattice time step (every stage of the hot path over all N nodes).
+The headline is FP32 on shifted populations; FP64 is measured on the same workload beside it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the single lattice is not partitioned:
+replicas only); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS (both distributions) & % HBM peak; batched-FP32 and adjoint vs plain FP64"
+UNIT = "GLUPS"
+N_NODES = 1 << 26
+S_E = 1.2
+AMP = 0.1
+# Algorithmic bytes per node-update: the six populations read and written once (FP32 / FP64).
+BYTES_PER_NODE = {"f32": 48, "f64": 96}
+WORKLOAD = "steepening acoustic wave, single periodic lattice N=2^26, lambda=1, s_e=1.2"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+_FIELDS = {}
+
+
+def workload_fields(N: int):
+    if N not in _FIELDS:
+        from paper_1802_02369_gb300 import workloads as W
+
+        _FIELDS[N] = W.steepening_wave(N, AMP, W.reference_pressure())
+    return _FIELDS[N]
+
+
+# ---------------------------------------------------------------------------------------------
+
+def cpu_oracle_rate(N_sample: int, budget_s: float, nthreads: int):
+    """Times the oracle (as it stands) on the first N_sample nodes of the workload, periodic,
+    for as many steps as fit about budget_s seconds. Returns (GLUPS, steps, seconds)."""
+    import oracle as O
+
+    ph = O.default_phys()
+    rho, u, p = workload_fields(N_SAMPLE_FULL)
+    rho, u, p = rho[:N_sample], u[:N_sample], p[:N_sample]
+    fd = O.init(ph, rho, u, p=p)
+    r = O.coupled_rates(S_E)
+    t0 = time.perf_counter()
+    fd = O.run(ph, r, fd, 1, nthreads)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    O.run(ph, r, fd, steps, nthreads)
+    dt = time.perf_counter() - t0
+    return N_sample * steps / dt / 1e9, steps, dt
+
+
+N_SAMPLE_FULL = N_NODES
+N_SAMPLE = 1 << 22
+
+
+def run_reference(args, rank: int):
+    """The CPU oracle as the reference arm (rank 0 only). Each benchmark step is one oracle time
+    step on a periodic sample of the workload's first n nodes, n sized from a calibration run so
+    that the whole run takes about two minutes."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    ph = O.default_phys()
+    r = O.coupled_rates(S_E)
+    rho, u, p = workload_fields(N_NODES)
+    cal_n = 1 << 20
+    fd = O.init(ph, rho[:cal_n], u[:cal_n], p=p[:cal_n])
+    t0 = time.perf_counter()
+    O.run(ph, r, fd, 2, cores)
+    rate = 2 * cal_n / (time.perf_counter() - t0)
+    nsteps = args.warmup + args.steps
+    n = int(min(1 << 22, max(4096, rate * 120.0 / max(1, nsteps))))
+    fd = O.init(ph, rho[:n], u[:n], p=p[:n])
+    fd = O.run(ph, r, fd, args.warmup, cores)
+    t0 = time.perf_counter()
+    O.run(ph, r, fd, args.steps, cores)   # the K timed steps in one oracle call
+    tsum = time.perf_counter() - t0
+    value = n * args.steps / tsum / 1e9
+    sample = f"first {n} nodes of the workload (periodic), {args.steps} oracle steps in one call, FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tsum / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_NODES, "precision": "f64 (CPU oracle)", "sample_nodes": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_device(lat, torch, steps: int, warmup: int, dist, world: int):
+    """Device-resident timing: K lattice steps between CUDA events on the library's stream."""
+    st = lat.stream
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    lat.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms
+
+
+def run_ours(args, rank: int, world: int, local: int, dist):
+    import torch
+
+    from paper_1802_02369_gb300 import build, lbm
+
+    torch.cuda.set_device(local)
+    build.build()
+    hbm_peak, peak_kind = measured_peaks()
+    rho, u, p = workload_fields(N_NODES)
+    d_rho, d_u, d_p = (torch.from_numpy(x).cuda() for x in (rho, u, p))
+    results = {}
+    with ClockSampler(local) as clk:
+        for prec in ("f32", "f64"):
+            lat = lbm.Lattice(N_NODES, s_e=S_E, precision=prec)
+            lat.set_state(d_rho, d_u, d_p)
+            k, nt = lat.autotune(2)
+            lat.set_state(d_rho, d_u, d_p)
+            steps = args.steps if prec == "f32" else max(8, min(args.steps, 200))
+            steps = ((steps + k - 1) // k) * k
+            ms = time_device(lat, torch, steps, max(args.warmup, 3) * k, dist, world)
+            launches = steps // k
+            glups = world * N_NODES * steps / (ms * 1e-3) / 1e9
+            launch_ms = ms / launches
+            alg_bytes = N_NODES * BYTES_PER_NODE[prec]          # one read + one write of the state
+            achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+            sums, flags, rc = lat.diagnostics()
+            results[prec] = dict(value=glups, ms_per_step=ms / steps, steps=steps, k=k, block_threads=nt,
+                                 launches=launches, launch_ms=launch_ms, achieved=achieved,
+                                 effective_gbs=glups / world * BYTES_PER_NODE[prec], flags=int(flags[0]))
+            lat.close()
+            torch.cuda.empty_cache()
+    clocks = clk.summary()
+
+    # End to end through the C-ABI with pinned host buffers: state in, K steps, (rho, J, zeta) out.
+    r32 = results["f32"]
+    K = r32["steps"]
+    h = [torch.from_numpy(x).pin_memory() for x in (rho, u, p)]
+    outs = [torch.empty(N_NODES, dtype=torch.float64).pin_memory() for _ in range(3)]
+    lat = lbm.Lattice(N_NODES, s_e=S_E, precision="f32")
+    lat.set_config(r32["k"], r32["block_threads"])
+    lat.set_state(*h)
+    lat.step(r32["k"] * 3)
+    lat.moments(out=outs + [None, None, None])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lat.set_state(*h)
+    lat.step(K)
+    lat.moments(out=outs + [None, None, None])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    lat.close()
+    e2e = {"value": world * N_NODES * K / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * 8 * N_NODES / K, "d2h_bytes_per_step": 3 * 8 * N_NODES / K}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        cores = os.cpu_count() or 1
+        g, st, dt = cpu_oracle_rate(N_SAMPLE, 15.0, cores)
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first 2^22 nodes of the workload (periodic), {st} steps, {dt:.1f} s, FP64"}
+
+    def roof(r, prec):
+        return {"bound": "hbm", "achieved": r["achieved"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": r["achieved"] / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": N_NODES * BYTES_PER_NODE[prec],
+                "steps_per_launch": r["k"], "launch_ms": r["launch_ms"],
+                "effective_gbs": r["effective_gbs"], "effective_frac": r["effective_gbs"] / hbm_peak}
+
+    f32, f64 = results["f32"], results["f64"]
+    line = {"metric": METRIC, "value": f32["value"], "unit": UNIT, "n_gpus": world, "steps": f32["steps"],
+            "warmup": max(args.warmup, 3) * f32["k"], "ms_per_step": f32["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_NODES, "precision": "f32 shifted populations",
+                       "steps_per_launch": f32["k"], "block_threads": f32["block_threads"],
+                       "l2": "inputs larger than L2 (FP32 state 1.6 GB, FP64 3.2 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof(f32, "f32"),
+            "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
+                     "roofline": roof(f64, "f64")},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
+            "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist_mod
+
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    run_ours(args, rank, world, local, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

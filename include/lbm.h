@@ -1,0 +1,152 @@
+/*
+ * C-ABI of the GB300 library for the coupled D1Q3Q3 entropy lattice Boltzmann scheme of
+ * Dubois, Graille and Lallemand, "Recovering the full Navier Stokes equations with lattice
+ * Boltzmann schemes" (sections 6 and 8). One "step" is the time iteration of section 8,
+ * steps (i)-(viii): moments m = M f_d (eq. M-d1q3q3), equilibria (eqs. energie-equilibre,
+ * psi-equilibre, eq-energie-entropie-d1q3q3) with the polytropic equation of state
+ * (eq. gaz-parfait), relaxation (eq. relaxation-d1q3q3) with the rates of step (iii), the
+ * entropy-production source of eq. (NS-rho-J-zeta), f_d* = M^{-1} m*, and streaming
+ * (eq. iteration-d1q3q3).
+ *
+ * Conventions
+ *  - Lattice units: dx = 1, dt = 1/lambda. A step does not depend on dx once nu = sigma_e lambda dx
+ *    (eq. nu-d1q3q3) and centred differences are used, so no dx is taken.
+ *  - A context holds B >= 1 independent lattices of lengths N[b], concatenated back to back
+ *    (lattice b occupies nodes offset[b] .. offset[b] + N[b] - 1, offset[0] = 0). Per-node arrays
+ *    passed to or returned from the library are float64 and indexed by that global node number.
+ *  - Pointers to per-node arrays may be host or device pointers (told apart with
+ *    cudaPointerGetAttributes). Host arrays are staged through a device buffer and the call
+ *    synchronises the stream before returning; device arrays are used in place and the call only
+ *    enqueues work on the context's stream (except where stated).
+ *  - All GPU work is enqueued on the stream given at creation (NULL = legacy default stream).
+ *  - Ownership: the library owns the context and its device state; the caller owns every array
+ *    it passes. Device memory is obtained through the allocator installed with
+ *    lbm_set_allocator (cudaMalloc/cudaFree if none).
+ *  - Every function returns LBM_OK (0) or a negative status; lbm_last_error(ctx) then describes it.
+ *    A failed call leaves the context usable unless the status is LBM_ERR_CUDA.
+ */
+#ifndef LBM_D1Q3Q3_H
+#define LBM_D1Q3Q3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1) /* N < 3, lambda <= 0, a rate outside (0, 2), unknown bc ... */
+#define LBM_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define LBM_ERR_OOM (-3)         /* the allocator returned NULL */
+#define LBM_ERR_UNSTABLE (-4)    /* diagnostics found a non-finite value, rho <= 0 or T <= 0 */
+#define LBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired */
+#define LBM_ERR_IO (-6)          /* checkpoint file could not be written or read, or mismatched */
+
+/* Boundary conditions (per lattice). Periodic is the paper's (section 9). Bounce-back is not in
+ * the paper: halfway bounce-back at both ends, f+(0) <- f-*(0), f-(N-1) <- f+*(N-1) (same for g),
+ * with source ghosts u_{-1} = -u_0, T_{-1} = T_0 (an adiabatic no-slip wall), mirrored at the
+ * right end. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+
+/* Storage/arithmetic precision of the populations.
+ * LBM_F64: FP64 storage and arithmetic.
+ * LBM_F32_SHIFTED: FP32 storage and arithmetic of the shifted populations f - w, where w are the
+ *   populations of the rest state (rho0, u = 0, s = s0) (the same shift is used in FP64). */
+enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1 };
+
+/* Relaxation rates of step (iii). s_e is the free rate (eq. henon-d1q3q3, nu = sigma_e lambda dx).
+ * s_psi <= 0 selects the coupling of eq. (lien-sigma-sigma), sigma_psi = (3/2)(gamma/Pr) sigma_e.
+ * s_eps <= 0 selects s_eps = 1.5 (sections 4 and 8). Every rate used must lie in (0, 2). */
+typedef struct {
+  double s_e, s_psi, s_eps;
+} lbm_rates;
+
+/* Physical constants shared by all lattices of a context. A NULL lbm_phys selects the section 9
+ * values: gamma = 1.4, Pr = 1, c_p = 1, rho0 = 1, s0 = 0, p0 = rho0 c0^2 / gamma with
+ * c0 = lambda / 2, source on. p0 <= 0 selects that p0 as well. rho0 is both the scale of M
+ * (eq. M-d1q3q3) and the reference density of eq. (gaz-parfait); s0 its reference entropy. */
+typedef struct {
+  double gamma, Pr, cp, rho0, p0, s0;
+  int32_t source_on; /* 1: entropy-production source of eq. (NS-rho-J-zeta); 0: off */
+  int32_t reserved;  /* must be 0 */
+} lbm_phys;
+
+/* Device allocator used for all device memory of contexts created afterwards.
+ * alloc(bytes, stream, user) returns a device pointer or NULL; free(ptr, user) releases it.
+ * Passing NULL for both restores cudaMalloc/cudaFree. Not thread-safe with concurrent creates. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, void *user);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *user);
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* One periodic or bounce-back lattice of N >= 3 nodes. rates: one lbm_rates. precision: LBM_F64 or
+ * LBM_F32_SHIFTED. phys: NULL for the section 9 defaults. stream: a cudaStream_t or NULL.
+ * The state is undefined until lbm_set_state (or lbm_load / lbm_set_populations). */
+int lbm_create(lbm_ctx **out, int64_t N, double lambda, const lbm_rates *rates, int32_t bc,
+               int32_t precision, const lbm_phys *phys, void *stream);
+
+/* B >= 1 independent lattices in one context (host arrays): N[B] lengths (each >= 3), rates[B],
+ * bc[B], s0[B] per-lattice reference entropy of eq. (gaz-parfait) (NULL: phys->s0 for all).
+ * Lattices advance together in one kernel per launch (ragged tiles, no inter-lattice coupling). */
+int lbm_create_batch(lbm_ctx **out, int32_t B, const int64_t *N, double lambda, const lbm_rates *rates,
+                     const int32_t *bc, const double *s0, int32_t precision, const lbm_phys *phys,
+                     void *stream);
+
+void lbm_destroy(lbm_ctx *ctx);
+const char *lbm_last_error(const lbm_ctx *ctx);
+int64_t lbm_total_nodes(const lbm_ctx *ctx);  /* sum of N[b] */
+int64_t lbm_steps_done(const lbm_ctx *ctx);   /* time steps taken since the last state set/load */
+
+/* Equilibrium initial state f_d = M^{-1} m_eq(rho, J = rho u, zeta = rho s) from per-node rho, u
+ * and pressure p (the specific entropy s follows from eq. (gaz-parfait)). Arrays of
+ * lbm_total_nodes() float64, host or device. Resets the step counter. */
+int lbm_set_state(lbm_ctx *ctx, const double *rho, const double *u, const double *p);
+/* Same from rho, u and the specific entropy s. */
+int lbm_set_state_entropy(lbm_ctx *ctx, const double *rho, const double *u, const double *s);
+
+/* Advances every lattice by nsteps >= 0 time steps (enqueued; no synchronisation). */
+int lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Moments m = (rho, J, zeta, e, psi, eps) per node (eq. M-d1q3q3) of the current state, each into a
+ * caller array of lbm_total_nodes() float64 (host or device); any pointer may be NULL. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *J, double *zeta, double *e, double *psi,
+                double *eps);
+
+/* Raw populations as float64, plane-major [6][lbm_total_nodes()] in the order
+ * (f0, f+, f-, g0, g+, g-) (the shift of LBM_F32_SHIFTED removed), host or device. */
+int lbm_get_populations(lbm_ctx *ctx, double *fd);
+/* Sets the populations from the same layout (rounded to FP32 for LBM_F32_SHIFTED after shifting). */
+int lbm_set_populations(lbm_ctx *ctx, const double *fd);
+
+/* Per-lattice FP64 sums, deterministic (fixed reduction order): sums[4 b + k] for k = 0..3 is
+ * sum rho, sum J, sum zeta and sum of the total energy p/(gamma-1) + rho u^2/2 over lattice b;
+ * flags[b] has bit 0 for a non-finite population, bit 1 for rho <= 0, bit 2 for T <= 0.
+ * Host arrays (B * 4 and B entries); synchronises. Returns LBM_ERR_UNSTABLE if any flag is set
+ * (the arrays are still filled). */
+int lbm_diagnostics(lbm_ctx *ctx, double *sums, int32_t *flags);
+
+/* Kernel configuration: steps_per_launch k in {1, 2, 4, 8} (temporal blocking: k steps per HBM
+ * round trip, 2k halo nodes per tile side) and block_threads in {256, 512, 1024} (tile width).
+ * 0 keeps the current value. */
+int lbm_set_config(lbm_ctx *ctx, int32_t steps_per_launch, int32_t block_threads);
+int lbm_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch, int32_t *block_threads);
+
+/* Times every (k, block_threads) pair on the current state (which is left unchanged; each trial
+ * writes only the second buffer) and keeps the fastest per node-update. trials >= 1 timed
+ * launches per candidate. Synchronises. Needs a state. */
+int lbm_autotune(lbm_ctx *ctx, int32_t trials);
+
+/* Checkpoint: writes / reads the populations, step counter and parameters to a host file. A load
+ * must match the context's lattice lengths, precision and parameters exactly; the resumed run is
+ * bitwise identical to an uninterrupted one. Synchronises. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_D1Q3Q3_H */

@@ -1,0 +1,845 @@
+// C-ABI of the D1Q3Q3 library (declared in include/lbm.h): context management, parameter
+// derivation (step (iii) of section 8), equilibrium initialisation, moment read-back,
+// deterministic FP64 diagnostics and checkpoints. The time step itself is in lbm_step.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using lbm::Consts;
+using lbm::LatDev;
+
+namespace {
+
+constexpr int kChunk = 1024;       // nodes per diagnostics chunk
+constexpr int kDiagThreads = 256;  // 4 nodes per thread
+
+lbm_alloc_fn g_alloc = nullptr;
+lbm_free_fn g_free = nullptr;
+void* g_user = nullptr;
+
+// Physical constants in FP64 after defaults are applied.
+struct PhysD {
+  double gamma, Pr, cp, rho0, p0, s0, lam;
+  int source_on;
+  double r() const { return cp * (1.0 - 1.0 / gamma); }
+  double e_r() const { return 3.0 * p0 - 2.0 * lam * lam * rho0; }
+  double wf0() const { return 1.0 - p0 / (rho0 * lam * lam); }  // rest populations of f
+  double wf1() const { return p0 / (2.0 * rho0 * lam * lam); }
+};
+
+template <typename R>
+Consts<R> make_consts(const PhysD& p) {
+  Consts<R> c;
+  const double l = p.lam, l2 = l * l, af = p.rho0, ag = p.rho0 * p.cp;
+  c.rho0 = R(p.rho0);
+  c.lam = R(l);
+  c.two_lam2 = R(2.0 * l2);
+  c.inv_af = R(1.0 / af);
+  c.inv_af_l = R(1.0 / (af * l));
+  c.inv_af_l2 = R(1.0 / (af * l2));
+  c.af_l = R(af * l);
+  c.af_l2 = R(af * l2);
+  c.ag = R(ag);
+  c.ag_l = R(ag * l);
+  c.ag_l2 = R(ag * l2);
+  c.inv_ag = R(1.0 / ag);
+  c.inv_ag_l = R(1.0 / (ag * l));
+  c.inv_ag_l2 = R(1.0 / (ag * l2));
+  c.gamma = R(p.gamma);
+  c.inv_cp = R(1.0 / p.cp);
+  c.p0 = R(p.p0);
+  c.inv_r = R(1.0 / p.r());
+  c.e_r = R(p.e_r());
+  c.cp_log = R((1.0 - 1.0 / p.gamma) * p.cp);
+  c.cp_over_Pr = R(p.cp / p.Pr);
+  c.source_on = p.source_on;
+  return c;
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) return g_alloc(bytes, (void*)st, g_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_user);
+  else cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Small kernels.
+
+__device__ __forceinline__ int lattice_of_node(const LatDev* lat, int B, long long i) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (lat[mid].offset <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct InitArgs {
+  double rho0, p0, gamma, cp, lam, e_r, cp_log, wf0, wf1;
+};
+
+// Equilibrium populations from (rho, u, p) (from_p = 1) or (rho, u, s) (from_p = 0), computed in
+// FP64 and stored shifted by the rest populations.
+template <typename R>
+__global__ void init_kernel(const double* __restrict__ rho_in, const double* __restrict__ u_in,
+                            const double* __restrict__ x_in, int from_p, R* __restrict__ st,
+                            long long plane, const LatDev* __restrict__ lat, int B, InitArgs a) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const LatDev& d = lat[lattice_of_node(lat, B, i)];
+  const double rho = rho_in[i], u = u_in[i];
+  const double lnr = log(rho / a.rho0);
+  const double ds = from_p ? (a.cp / a.gamma) * log(x_in[i] / a.p0) - a.cp * lnr : x_in[i] - d.s0;
+  const double s = d.s0 + ds;
+  const double pt = a.p0 * expm1(a.gamma * (lnr + ds / a.cp));
+  const double rt = rho - a.rho0, J = rho * u;
+  const double zeta = rho * s, zt = zeta - d.zeta_r;
+  const double l2 = a.lam * a.lam;
+  const double e_t = 3.0 * (J * u + pt) - 2.0 * l2 * rt;
+  const double psi = zeta * u;
+  const double eps_t = 2.0 * l2 * rho * (ds + a.cp_log * lnr) + e_t * s + a.e_r * ds;
+  const double af = a.rho0, ag = a.rho0 * a.cp;
+  double r = rt / af, j = J / (af * a.lam), q = e_t / (af * l2);
+  st[0 * plane + i] = R((r - q) / 3.0);
+  st[1 * plane + i] = R((2.0 * r + q) / 6.0 + 0.5 * j);
+  st[2 * plane + i] = R((2.0 * r + q) / 6.0 - 0.5 * j);
+  r = zt / ag; j = psi / (ag * a.lam); q = eps_t / (ag * l2);
+  st[3 * plane + i] = R((r - q) / 3.0);
+  st[4 * plane + i] = R((2.0 * r + q) / 6.0 + 0.5 * j);
+  st[5 * plane + i] = R((2.0 * r + q) / 6.0 - 0.5 * j);
+}
+
+// Moments (absolute) per node; any output may be null.
+template <typename R>
+__global__ void moments_kernel(const R* __restrict__ st, long long plane, const LatDev* __restrict__ lat,
+                               int B, InitArgs a, double* rho, double* J, double* zeta, double* e,
+                               double* psi, double* eps) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const LatDev& d = lat[lattice_of_node(lat, B, i)];
+  double f[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) f[k] = (double)st[k * plane + i];
+  const double l = a.lam, af = a.rho0, ag = a.rho0 * a.cp;
+  if (rho) rho[i] = a.rho0 + af * (f[0] + f[1] + f[2]);
+  if (J) J[i] = af * l * (f[1] - f[2]);
+  if (e) e[i] = a.e_r + af * l * l * (f[1] + f[2] - 2.0 * f[0]);
+  if (zeta) zeta[i] = d.zeta_r + ag * (f[3] + f[4] + f[5]);
+  if (psi) psi[i] = ag * l * (f[4] - f[5]);
+  if (eps) eps[i] = d.eps_r + ag * l * l * (f[4] + f[5] - 2.0 * f[3]);
+}
+
+template <typename R>
+__global__ void pops_out_kernel(const R* __restrict__ st, long long plane, const LatDev* __restrict__ lat,
+                                int B, double wf0, double wf1, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const LatDev& d = lat[lattice_of_node(lat, B, i)];
+  const double w[6] = {wf0, wf1, wf1, d.wg0, d.wg1, d.wg1};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[k * plane + i] = (double)st[k * plane + i] + w[k];
+}
+
+template <typename R>
+__global__ void pops_in_kernel(R* __restrict__ st, long long plane, const LatDev* __restrict__ lat, int B,
+                               double wf0, double wf1, const double* __restrict__ in) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const LatDev& d = lat[lattice_of_node(lat, B, i)];
+  const double w[6] = {wf0, wf1, wf1, d.wg0, d.wg1, d.wg1};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) st[k * plane + i] = R(in[k * plane + i] - w[k]);
+}
+
+// Diagnostics, pass 1: one block per chunk of kChunk nodes of one lattice; fixed-order reduction.
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) diag_chunk_kernel(const R* __restrict__ st, long long plane,
+                                                                  const LatDev* __restrict__ lat, int B, InitArgs a,
+                                                                  double gamma, double inv_r,
+                                                                  double* __restrict__ part,
+                                                                  int* __restrict__ pflag) {
+  const long long chunk = blockIdx.x;
+  int L = 0;
+  {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (lat[mid].chunk0 <= chunk) lo = mid; else hi = mid - 1;
+    }
+    L = lo;
+  }
+  const LatDev& d = lat[L];
+  const long long base = (chunk - d.chunk0) * kChunk;
+  double acc[4] = {0, 0, 0, 0};
+  int fl = 0;
+  const double l = a.lam, af = a.rho0, ag = a.rho0 * a.cp;
+  for (int t = 0; t < kChunk / kDiagThreads; ++t) {
+    const long long pos = base + t * kDiagThreads + threadIdx.x;
+    if (pos >= d.n) break;
+    const long long i = d.offset + pos;
+    double f[6];
+    for (int k = 0; k < 6; ++k) {
+      f[k] = (double)st[k * plane + i];
+      if (!isfinite(f[k])) fl |= 1;
+    }
+    const double rt = af * (f[0] + f[1] + f[2]);
+    const double rho = a.rho0 + rt;
+    const double J = af * l * (f[1] - f[2]);
+    const double zt = ag * (f[3] + f[4] + f[5]);
+    const double u = J / rho;
+    const double ds = (zt - rt * d.s0) / rho;
+    const double p = a.p0 * exp(gamma * (log(rho / a.rho0) + ds / a.cp));
+    const double T = p / rho * inv_r;
+    if (!(rho > 0.0)) fl |= 2;
+    if (!(T > 0.0) || !isfinite(T)) fl |= 4;
+    acc[0] += rho;
+    acc[1] += J;
+    acc[2] += d.zeta_r + zt;
+    acc[3] += p / (gamma - 1.0) + 0.5 * rho * u * u;
+  }
+  __shared__ double sh[4][kDiagThreads / 32];
+  __shared__ int shf[kDiagThreads / 32];
+  for (int k = 0; k < 4; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+  }
+  int f2 = fl;
+  for (int o = 16; o > 0; o >>= 1) f2 |= __shfl_down_sync(0xffffffffu, f2, o);
+  if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = f2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < kDiagThreads / 32; ++w) v += sh[k][w];
+      part[chunk * 4 + k] = v;
+    }
+    int ff = 0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) ff |= shf[w];
+    pflag[chunk] = ff;
+  }
+}
+
+// Diagnostics, pass 2: one block per lattice sums its chunks in a fixed order.
+__global__ void __launch_bounds__(256) diag_final_kernel(const double* __restrict__ part, const int* __restrict__ pflag,
+                                                         const LatDev* __restrict__ lat, int B, long long nchunks,
+                                                         double* __restrict__ sums, int* __restrict__ flags) {
+  const int L = blockIdx.x;
+  const long long c0 = lat[L].chunk0;
+  const long long c1 = (L + 1 < B) ? lat[L + 1].chunk0 : nchunks;
+  double acc[4] = {0, 0, 0, 0};
+  int fl = 0;
+  for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    for (int k = 0; k < 4; ++k) acc[k] += part[c * 4 + k];
+    fl |= pflag[c];
+  }
+  __shared__ double sh[4][8];
+  __shared__ int shf[8];
+  for (int k = 0; k < 4; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = v;
+  }
+  int f2 = fl;
+  for (int o = 16; o > 0; o >>= 1) f2 |= __shfl_down_sync(0xffffffffu, f2, o);
+  if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = f2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < 8; ++w) v += sh[k][w];
+      sums[L * 4 + k] = v;
+    }
+    int ff = 0;
+    for (int w = 0; w < 8; ++w) ff |= shf[w];
+    flags[L] = ff;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Context.
+
+struct lbm_ctx {
+  int B = 0;
+  long long Ntot = 0;
+  int precision = LBM_F64;
+  PhysD ph{};
+  cudaStream_t stream = nullptr;
+  std::vector<long long> N, offset;
+  std::vector<lbm_rates> rates;
+  std::vector<int> bc;
+  std::vector<double> s0;
+  std::vector<LatDev> host_lat;     // tile0 of table k (k = 0..3 for depth 1, 2, 4, 8) lives in
+  std::vector<LatDev> host_tabs;    //   host_tabs[k * B .. k * B + B - 1]
+  LatDev* d_lat = nullptr;          // 4 * B records on the device, same layout
+  long long ntiles_k[4] = {0, 0, 0, 0};
+  void* state[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool has_state = false;
+  long long ntiles = 0;
+  int K = 1, NT = 512;
+  long long nchunks = 0;
+  double* d_part = nullptr;
+  int* d_pflag = nullptr;
+  double* d_sums = nullptr;
+  int* d_flags = nullptr;
+  double* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  long long steps_done = 0;
+  std::string err;
+
+  size_t elem() const { return precision == LBM_F64 ? sizeof(double) : sizeof(float); }
+  size_t state_bytes() const { return 6 * (size_t)Ntot * elem(); }
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CK(ctx, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+InitArgs init_args(const lbm_ctx* c) {
+  InitArgs a;
+  a.rho0 = c->ph.rho0;
+  a.p0 = c->ph.p0;
+  a.gamma = c->ph.gamma;
+  a.cp = c->ph.cp;
+  a.lam = c->ph.lam;
+  a.e_r = c->ph.e_r();
+  a.cp_log = (1.0 - 1.0 / c->ph.gamma) * c->ph.cp;
+  a.wf0 = c->ph.wf0();
+  a.wf1 = c->ph.wf1();
+  return a;
+}
+
+inline int depth_index(int K) { return K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : 3; }
+
+// For tile width NT and each depth K in {1, 2, 4, 8}: index of each lattice's first tile (tiles of
+// NT - 4K output nodes); diagnostics chunk starts likewise (independent of the tiling).
+void rebuild_tables(lbm_ctx* c) {
+  c->host_tabs.resize(4 * (size_t)c->B);
+  long long ch = 0;
+  for (int b = 0; b < c->B; ++b) {
+    c->host_lat[b].chunk0 = ch;
+    ch += (c->N[b] + kChunk - 1) / kChunk;
+  }
+  c->nchunks = ch;
+  for (int ki = 0; ki < 4; ++ki) {
+    const long long bout = c->NT - 4 * (1 << ki);
+    long long t = 0;
+    for (int b = 0; b < c->B; ++b) {
+      LatDev d = c->host_lat[b];
+      d.tile0 = t;
+      c->host_tabs[ki * (size_t)c->B + b] = d;
+      t += bout > 0 ? (c->N[b] + bout - 1) / bout : 0;
+    }
+    c->ntiles_k[ki] = bout > 0 ? t : 0;
+  }
+  c->ntiles = c->ntiles_k[depth_index(c->K)];
+}
+
+int upload_lat(lbm_ctx* c) {
+  LBM_CK(c, cudaMemcpyAsync(c->d_lat, c->host_tabs.data(), sizeof(LatDev) * 4 * c->B, cudaMemcpyHostToDevice,
+                            c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));  // host_tabs may change again before the copy runs
+  return LBM_OK;
+}
+
+// Device table for depth K.
+inline const LatDev* lat_for(const lbm_ctx* c, int K) { return c->d_lat + depth_index(K) * (size_t)c->B; }
+
+int ensure_stage(lbm_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return LBM_OK;
+  dev_free(c->d_stage);
+  c->d_stage = (double*)dev_alloc(bytes, c->stream);
+  c->stage_bytes = c->d_stage ? bytes : 0;
+  if (!c->d_stage) return fail(c, LBM_ERR_OOM, "staging buffer allocation failed");
+  return LBM_OK;
+}
+
+bool valid_rate(double s) { return s > 0.0 && s < 2.0; }
+
+int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_rates* rates, const int32_t* bc,
+              const double* s0, int precision, const lbm_phys* phys, void* stream) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (B < 1 || !N || !rates || !bc || !(lambda > 0.0) || !std::isfinite(lambda)) return LBM_ERR_INVALID_ARG;
+  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED) return LBM_ERR_INVALID_ARG;
+  PhysD ph;
+  ph.lam = lambda;
+  ph.gamma = phys ? phys->gamma : 1.4;
+  ph.Pr = phys ? phys->Pr : 1.0;
+  ph.cp = phys ? phys->cp : 1.0;
+  ph.rho0 = phys ? phys->rho0 : 1.0;
+  ph.s0 = phys ? phys->s0 : 0.0;
+  ph.source_on = phys ? (phys->source_on != 0) : 1;
+  const double c0 = lambda / 2.0;
+  ph.p0 = (phys && phys->p0 > 0.0) ? phys->p0 : ph.rho0 * c0 * c0 / ph.gamma;
+  if (!(ph.gamma > 1.0) || !(ph.Pr > 0.0) || !(ph.cp > 0.0) || !(ph.rho0 > 0.0) || !(ph.p0 > 0.0))
+    return LBM_ERR_INVALID_ARG;
+  if (phys && phys->reserved != 0) return LBM_ERR_INVALID_ARG;
+
+  lbm_ctx* c = new lbm_ctx();
+  c->B = B;
+  c->precision = precision;
+  c->ph = ph;
+  c->stream = (cudaStream_t)stream;
+  c->N.resize(B);
+  c->offset.resize(B + 1);
+  c->rates.resize(B);
+  c->bc.resize(B);
+  c->s0.resize(B);
+  c->host_lat.resize(B);
+  long long tot = 0;
+  for (int b = 0; b < B; ++b) {
+    if (N[b] < 3 || (bc[b] != LBM_BC_PERIODIC && bc[b] != LBM_BC_BOUNCEBACK)) { delete c; return LBM_ERR_INVALID_ARG; }
+    lbm_rates r = rates[b];
+    if (!valid_rate(r.s_e)) { delete c; return LBM_ERR_INVALID_ARG; }
+    const double sigma_e = 1.0 / r.s_e - 0.5;
+    if (!(r.s_psi > 0.0)) r.s_psi = 1.0 / (1.5 * (ph.gamma / ph.Pr) * sigma_e + 0.5);  // eq. lien-sigma-sigma
+    if (!(r.s_eps > 0.0)) r.s_eps = 1.5;
+    if (!valid_rate(r.s_psi) || !valid_rate(r.s_eps)) { delete c; return LBM_ERR_INVALID_ARG; }
+    c->N[b] = N[b];
+    c->offset[b] = tot;
+    c->rates[b] = r;
+    c->bc[b] = bc[b];
+    c->s0[b] = s0 ? s0[b] : ph.s0;
+    LatDev& d = c->host_lat[b];
+    d.offset = tot;
+    d.n = N[b];
+    d.s_e = r.s_e;
+    d.s_psi = r.s_psi;
+    d.s_eps = r.s_eps;
+    d.q_src = 0.25 * sigma_e;
+    d.s0 = c->s0[b];
+    d.zeta_r = ph.rho0 * d.s0;
+    d.eps_r = ph.e_r() * d.s0;
+    // Rest g populations M_g^{-1}(zeta_r, 0, eps_r).
+    {
+      const double r0 = d.zeta_r / (ph.rho0 * ph.cp), q0 = d.eps_r / (ph.rho0 * ph.cp * lambda * lambda);
+      d.wg0 = (r0 - q0) / 3.0;
+      d.wg1 = (2.0 * r0 + q0) / 6.0;
+    }
+    d.bc = bc[b];
+    d.pad = 0;
+    tot += N[b];
+  }
+  c->offset[B] = tot;
+  c->Ntot = tot;
+  c->K = (precision == LBM_F64) ? 1 : 4;
+  c->NT = (precision == LBM_F64) ? 512 : 1024;
+  rebuild_tables(c);
+
+  c->d_lat = (LatDev*)dev_alloc(sizeof(LatDev) * 4 * B, c->stream);
+  c->state[0] = dev_alloc(c->state_bytes(), c->stream);
+  c->state[1] = dev_alloc(c->state_bytes(), c->stream);
+  c->d_sums = (double*)dev_alloc(sizeof(double) * 4 * B, c->stream);
+  c->d_flags = (int*)dev_alloc(sizeof(int) * B, c->stream);
+  c->d_part = (double*)dev_alloc(sizeof(double) * 4 * c->nchunks, c->stream);
+  c->d_pflag = (int*)dev_alloc(sizeof(int) * c->nchunks, c->stream);
+  if (!c->d_lat || !c->state[0] || !c->state[1] || !c->d_sums || !c->d_flags || !c->d_part || !c->d_pflag) {
+    lbm_destroy(c);
+    return LBM_ERR_OOM;
+  }
+  if (upload_lat(c) != LBM_OK) {
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+template <typename R>
+int run_steps(lbm_ctx* c, long long nsteps) {
+  const Consts<R> k = make_consts<R>(c->ph);
+  long long left = nsteps;
+  while (left > 0) {
+    int K = c->K;
+    while (K > left) K >>= 1;  // the remainder runs with shallower launches (same arithmetic)
+    const int ki = depth_index(K);
+    cudaError_t e = lbm::launch_step_tiles<R>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot,
+                                              lat_for(c, K), c->B, c->ntiles_k[ki], K, c->NT, k, c->stream, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    c->cur = 1 - c->cur;
+    left -= K;
+    c->steps_done += K;
+  }
+  return LBM_OK;
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int set_state_impl(lbm_ctx* c, const double* rho, const double* u, const double* x, int from_p) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (!rho || !u || !x) return fail(c, LBM_ERR_INVALID_ARG, "set_state: null array");
+  const long long n = c->Ntot;
+  const double *dr = rho, *du = u, *dx = x;
+  const bool host = !is_device_ptr(rho);
+  if (host != !is_device_ptr(u) || host != !is_device_ptr(x))
+    return fail(c, LBM_ERR_INVALID_ARG, "set_state: mix of host and device arrays");
+  if (host) {
+    int rc = ensure_stage(c, 3 * sizeof(double) * n);
+    if (rc) return rc;
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage, rho, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage + n, u, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage + 2 * n, x, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    dr = c->d_stage;
+    du = c->d_stage + n;
+    dx = c->d_stage + 2 * n;
+  }
+  const InitArgs a = init_args(c);
+  if (c->precision == LBM_F64)
+    init_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(dr, du, dx, from_p, (double*)c->state[c->cur], n,
+                                                                    c->d_lat, c->B, a);
+  else
+    init_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(dr, du, dx, from_p, (float*)c->state[c->cur], n,
+                                                                   c->d_lat, c->B, a);
+  LBM_CK(c, cudaGetLastError());
+  if (host) LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->has_state = true;
+  c->steps_done = 0;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Exported entry points.
+
+extern "C" {
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return LBM_ERR_INVALID_ARG;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_user = user;
+  return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, int64_t N, double lambda, const lbm_rates* rates, int32_t bc, int32_t precision,
+               const lbm_phys* phys, void* stream) {
+  return do_create(out, 1, &N, lambda, rates, &bc, nullptr, precision, phys, stream);
+}
+
+int lbm_create_batch(lbm_ctx** out, int32_t B, const int64_t* N, double lambda, const lbm_rates* rates,
+                     const int32_t* bc, const double* s0, int32_t precision, const lbm_phys* phys, void* stream) {
+  return do_create(out, B, N, lambda, rates, bc, s0, precision, phys, stream);
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  dev_free(c->d_lat);
+  dev_free(c->state[0]);
+  dev_free(c->state[1]);
+  dev_free(c->d_sums);
+  dev_free(c->d_flags);
+  dev_free(c->d_part);
+  dev_free(c->d_pflag);
+  dev_free(c->d_stage);
+  delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+int64_t lbm_total_nodes(const lbm_ctx* c) { return c ? c->Ntot : -1; }
+int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps_done : -1; }
+
+int lbm_set_state(lbm_ctx* c, const double* rho, const double* u, const double* p) {
+  return set_state_impl(c, rho, u, p, 1);
+}
+
+int lbm_set_state_entropy(lbm_ctx* c, const double* rho, const double* u, const double* s) {
+  return set_state_impl(c, rho, u, s, 0);
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "step: nsteps < 0");
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "step: no state set");
+  return c->precision == LBM_F64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* J, double* zeta, double* e, double* psi, double* eps) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "moments: no state set");
+  double* outs[6] = {rho, J, zeta, e, psi, eps};
+  int host = -1;
+  for (double* p : outs) {
+    if (!p) continue;
+    const int h = is_device_ptr(p) ? 0 : 1;
+    if (host >= 0 && h != host) return fail(c, LBM_ERR_INVALID_ARG, "moments: mix of host and device arrays");
+    host = h;
+  }
+  if (host < 0) return LBM_OK;
+  const long long n = c->Ntot;
+  double* dst[6];
+  if (host) {
+    int cnt = 0;
+    for (double* p : outs) cnt += p != nullptr;
+    int rc = ensure_stage(c, sizeof(double) * n * cnt);
+    if (rc) return rc;
+    int k = 0;
+    for (int i = 0; i < 6; ++i) dst[i] = outs[i] ? c->d_stage + (k++) * n : nullptr;
+  } else {
+    for (int i = 0; i < 6; ++i) dst[i] = outs[i];
+  }
+  const InitArgs a = init_args(c);
+  if (c->precision == LBM_F64)
+    moments_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->d_lat, c->B,
+                                                                       a, dst[0], dst[1], dst[2], dst[3], dst[4], dst[5]);
+  else
+    moments_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float*)c->state[c->cur], n, c->d_lat, c->B,
+                                                                      a, dst[0], dst[1], dst[2], dst[3], dst[4], dst[5]);
+  LBM_CK(c, cudaGetLastError());
+  if (host) {
+    for (int i = 0; i < 6; ++i)
+      if (outs[i]) LBM_CK(c, cudaMemcpyAsync(outs[i], dst[i], sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* fd) {
+  if (!c || !fd) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "populations: no state set");
+  const long long n = c->Ntot;
+  const bool host = !is_device_ptr(fd);
+  double* dst = fd;
+  if (host) {
+    int rc = ensure_stage(c, 6 * sizeof(double) * n);
+    if (rc) return rc;
+    dst = c->d_stage;
+  }
+  const double wf0 = c->ph.wf0(), wf1 = c->ph.wf1();
+  if (c->precision == LBM_F64)
+    pops_out_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->d_lat,
+                                                                        c->B, wf0, wf1, dst);
+  else
+    pops_out_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float*)c->state[c->cur], n, c->d_lat, c->B,
+                                                                       wf0, wf1, dst);
+  LBM_CK(c, cudaGetLastError());
+  if (host) {
+    LBM_CK(c, cudaMemcpyAsync(fd, dst, 6 * sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* fd) {
+  if (!c || !fd) return LBM_ERR_INVALID_ARG;
+  const long long n = c->Ntot;
+  const bool host = !is_device_ptr(fd);
+  const double* src = fd;
+  if (host) {
+    int rc = ensure_stage(c, 6 * sizeof(double) * n);
+    if (rc) return rc;
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage, fd, 6 * sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    src = c->d_stage;
+  }
+  const double wf0 = c->ph.wf0(), wf1 = c->ph.wf1();
+  if (c->precision == LBM_F64)
+    pops_in_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((double*)c->state[c->cur], n, c->d_lat, c->B, wf0,
+                                                                       wf1, src);
+  else
+    pops_in_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>((float*)c->state[c->cur], n, c->d_lat, c->B, wf0,
+                                                                      wf1, src);
+  LBM_CK(c, cudaGetLastError());
+  if (host) LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->has_state = true;
+  c->steps_done = 0;
+  return LBM_OK;
+}
+
+int lbm_diagnostics(lbm_ctx* c, double* sums, int32_t* flags) {
+  if (!c || !sums || !flags) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "diagnostics: no state set");
+  const InitArgs a = init_args(c);
+  const double inv_r = 1.0 / c->ph.r();
+  if (c->nchunks > 0) {
+    if (c->precision == LBM_F64)
+      diag_chunk_kernel<double><<<(unsigned)c->nchunks, kDiagThreads, 0, c->stream>>>(
+          (const double*)c->state[c->cur], c->Ntot, c->d_lat, c->B, a, c->ph.gamma, inv_r, c->d_part, c->d_pflag);
+    else
+      diag_chunk_kernel<float><<<(unsigned)c->nchunks, kDiagThreads, 0, c->stream>>>(
+          (const float*)c->state[c->cur], c->Ntot, c->d_lat, c->B, a, c->ph.gamma, inv_r, c->d_part, c->d_pflag);
+    LBM_CK(c, cudaGetLastError());
+  }
+  diag_final_kernel<<<c->B, 256, 0, c->stream>>>(c->d_part, c->d_pflag, c->d_lat, c->B, c->nchunks, c->d_sums,
+                                                   c->d_flags);
+  LBM_CK(c, cudaGetLastError());
+  LBM_CK(c, cudaMemcpyAsync(sums, c->d_sums, sizeof(double) * 4 * c->B, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaMemcpyAsync(flags, c->d_flags, sizeof(int) * c->B, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < c->B; ++b)
+    if (flags[b]) return fail(c, LBM_ERR_UNSTABLE, "diagnostics: lattice " + std::to_string(b) + " flagged (flags=" +
+                                                       std::to_string(flags[b]) + ")");
+  return LBM_OK;
+}
+
+int lbm_set_config(lbm_ctx* c, int32_t k, int32_t nt) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (k != 0 && k != 1 && k != 2 && k != 4 && k != 8) return fail(c, LBM_ERR_INVALID_ARG, "config: k not in {1,2,4,8}");
+  if (nt != 0 && nt != 256 && nt != 512 && nt != 1024)
+    return fail(c, LBM_ERR_INVALID_ARG, "config: block_threads not in {256,512,1024}");
+  const int newK = k ? k : c->K, newNT = nt ? nt : c->NT;
+  if (newNT - 4 * newK < 32) return fail(c, LBM_ERR_INVALID_ARG, "config: tile too narrow for depth");
+  // Diagnostics scratch depends only on the lattices; tile tables on (k, NT).
+  c->K = newK;
+  c->NT = newNT;
+  rebuild_tables(c);
+  return upload_lat(c);
+}
+
+int lbm_get_config(const lbm_ctx* c, int32_t* k, int32_t* nt) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (k) *k = c->K;
+  if (nt) *nt = c->NT;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx* c, int32_t trials) {
+  if (!c || trials < 1) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "autotune: no state set");
+  cudaEvent_t e0, e1;
+  LBM_CK(c, cudaEventCreate(&e0));
+  LBM_CK(c, cudaEventCreate(&e1));
+  const int Ks[4] = {1, 2, 4, 8};
+  const int NTs[3] = {256, 512, 1024};
+  double best = 1e300;
+  int bestK = c->K, bestNT = c->NT;
+  for (int nt : NTs)
+    for (int k : Ks) {
+      if (nt - 4 * k < 32) continue;
+      c->K = k;
+      c->NT = nt;
+      rebuild_tables(c);
+      int rc = upload_lat(c);
+      if (rc) return rc;
+      float ms = 0.f;
+      for (int t = 0; t <= trials; ++t) {  // first launch is a warm-up
+        if (t == 1) LBM_CK(c, cudaEventRecord(e0, c->stream));
+        cudaError_t e;
+        if (c->precision == LBM_F64)
+          e = lbm::launch_step_tiles<double>((const double*)c->state[c->cur], (double*)c->state[1 - c->cur], c->Ntot,
+                                             lat_for(c, k), c->B, c->ntiles, k, nt, make_consts<double>(c->ph),
+                                             c->stream, 0);
+        else
+          e = lbm::launch_step_tiles<float>((const float*)c->state[c->cur], (float*)c->state[1 - c->cur], c->Ntot,
+                                            lat_for(c, k), c->B, c->ntiles, k, nt, make_consts<float>(c->ph),
+                                            c->stream, 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
+      }
+      LBM_CK(c, cudaEventRecord(e1, c->stream));
+      LBM_CK(c, cudaEventSynchronize(e1));
+      LBM_CK(c, cudaEventElapsedTime(&ms, e0, e1));
+      const double per_step = ms / (double)(trials * k);
+      if (per_step < best) { best = per_step; bestK = k; bestNT = nt; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->K = bestK;
+  c->NT = bestNT;
+  rebuild_tables(c);
+  return upload_lat(c);
+}
+
+// Checkpoint format: magic, version, precision, B, the physical constants, per-lattice
+// (N, rates, bc, s0), the step counter, then the raw state bytes (shifted populations, plane-major).
+static const char kMagic[8] = {'L', 'B', 'M', 'D', '1', 'Q', '3', '3'};
+
+int lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !path) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "save: no state set");
+  std::vector<char> buf(c->state_bytes());
+  LBM_CK(c, cudaMemcpyAsync(buf.data(), c->state[c->cur], buf.size(), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, LBM_ERR_IO, std::string("save: cannot open ") + path);
+  const int32_t ver = 1, prec = c->precision, B = c->B;
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&ver, 4, 1, f) == 1 && std::fwrite(&prec, 4, 1, f) == 1 &&
+            std::fwrite(&B, 4, 1, f) == 1 && std::fwrite(&c->ph, sizeof(PhysD), 1, f) == 1;
+  for (int b = 0; ok && b < c->B; ++b) {
+    const int64_t n = c->N[b];
+    const int32_t bcv = c->bc[b];
+    ok = std::fwrite(&n, 8, 1, f) == 1 && std::fwrite(&c->rates[b], sizeof(lbm_rates), 1, f) == 1 &&
+         std::fwrite(&bcv, 4, 1, f) == 1 && std::fwrite(&c->s0[b], 8, 1, f) == 1;
+  }
+  const int64_t steps = c->steps_done;
+  ok = ok && std::fwrite(&steps, 8, 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? LBM_OK : fail(c, LBM_ERR_IO, "save: write failed");
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !path) return LBM_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, LBM_ERR_IO, std::string("load: cannot open ") + path);
+  char magic[8];
+  int32_t ver = 0, prec = -1, B = 0;
+  PhysD ph;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 && std::fread(&ver, 4, 1, f) == 1 &&
+            ver == 1 && std::fread(&prec, 4, 1, f) == 1 && prec == c->precision && std::fread(&B, 4, 1, f) == 1 &&
+            B == c->B && std::fread(&ph, sizeof(PhysD), 1, f) == 1 && std::memcmp(&ph, &c->ph, sizeof(PhysD)) == 0;
+  for (int b = 0; ok && b < c->B; ++b) {
+    int64_t n;
+    lbm_rates r;
+    int32_t bcv;
+    double s0;
+    ok = std::fread(&n, 8, 1, f) == 1 && n == c->N[b] && std::fread(&r, sizeof(lbm_rates), 1, f) == 1 &&
+         std::memcmp(&r, &c->rates[b], sizeof(lbm_rates)) == 0 && std::fread(&bcv, 4, 1, f) == 1 && bcv == c->bc[b] &&
+         std::fread(&s0, 8, 1, f) == 1 && s0 == c->s0[b];
+  }
+  int64_t steps = 0;
+  std::vector<char> buf(c->state_bytes());
+  ok = ok && std::fread(&steps, 8, 1, f) == 1 && std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return fail(c, LBM_ERR_IO, "load: file does not match this context");
+  LBM_CK(c, cudaMemcpyAsync(c->state[c->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  c->has_state = true;
+  c->steps_done = steps;
+  return LBM_OK;
+}
+
+}  // extern "C"

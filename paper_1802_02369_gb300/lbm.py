@@ -1,0 +1,293 @@
+"""Python binding of the C-ABI in include/lbm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/liblbm.so``; this module loads it with
+ctypes, installs PyTorch's caching allocator as the library's device allocator, and passes torch
+streams and tensor pointers through. There is no fallback: if the library is missing or CUDA is
+unavailable, the calls raise.
+
+Function names follow the C-ABI (``lbm_create`` ...); :class:`Lattice` wraps a context.
+Arrays may be numpy arrays (host memory, staged by the library) or torch tensors (device or host).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lbm.h")
+
+LBM_OK = 0
+LBM_ERR_INVALID_ARG = -1
+LBM_ERR_CUDA = -2
+LBM_ERR_OOM = -3
+LBM_ERR_UNSTABLE = -4
+LBM_ERR_TIMEOUT = -5
+LBM_ERR_IO = -6
+LBM_BC_PERIODIC = 0
+LBM_BC_BOUNCEBACK = 1
+LBM_F64 = 0
+LBM_F32_SHIFTED = 1
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class lbm_rates(ctypes.Structure):
+    _fields_ = [("s_e", ctypes.c_double), ("s_psi", ctypes.c_double), ("s_eps", ctypes.c_double)]
+
+
+class lbm_phys(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("cp", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("p0", ctypes.c_double), ("s0", ctypes.c_double),
+                ("source_on", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_callbacks = []
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/lbm.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", txt)) - {"lbm_alloc_fn", "lbm_free_fn"})
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads liblbm.so and declares the signatures (no CUDA call is made)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"liblbm.so not built ({path}); run paper_1802_02369_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        i32, i64, d, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        P = ctypes.POINTER
+        sig = {
+            "lbm_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+            "lbm_create": (i32, [P(vp), i64, d, P(lbm_rates), i32, i32, P(lbm_phys), vp]),
+            "lbm_create_batch": (i32, [P(vp), i32, P(i64), d, P(lbm_rates), P(i32), P(d), i32, P(lbm_phys), vp]),
+            "lbm_destroy": (None, [vp]),
+            "lbm_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_total_nodes": (i64, [vp]),
+            "lbm_steps_done": (i64, [vp]),
+            "lbm_set_state": (i32, [vp, vp, vp, vp]),
+            "lbm_set_state_entropy": (i32, [vp, vp, vp, vp]),
+            "lbm_step": (i32, [vp, i64]),
+            "lbm_moments": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+            "lbm_get_populations": (i32, [vp, vp]),
+            "lbm_set_populations": (i32, [vp, vp]),
+            "lbm_diagnostics": (i32, [vp, P(d), P(i32)]),
+            "lbm_set_config": (i32, [vp, i32, i32]),
+            "lbm_get_config": (i32, [vp, P(i32), P(i32)]),
+            "lbm_autotune": (i32, [vp, i32]),
+            "lbm_save": (i32, [vp, ctypes.c_char_p]),
+            "lbm_load": (i32, [vp, ctypes.c_char_p]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("CUDA is not available: the D1Q3Q3 library runs on the GPU only")
+    return torch
+
+
+def install_torch_allocator():
+    """Routes the library's device allocations through torch's caching allocator."""
+    torch = _torch()
+    lib = load_library()
+    if _callbacks:
+        return
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:  # out of memory: the library reports LBM_ERR_OOM
+            return None
+
+    def _free(ptr, user):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _callbacks.extend([a, f])
+    rc = lib.lbm_set_allocator(a, f, None)
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_set_allocator failed")
+
+
+class _Arr:
+    """A host or device float64 array passed by pointer; keeps the owner alive."""
+
+    def __init__(self, x, n: int, writable: bool = False):
+        torch = None
+        try:
+            import torch as _t
+            torch = _t
+        except ImportError:
+            pass
+        if torch is not None and isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != n:
+                raise ValueError(f"expected a contiguous float64 tensor of {n} elements")
+            self.obj, self.ptr = x, x.data_ptr()
+        else:
+            a = np.asarray(x)
+            if writable:
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+                    raise ValueError(f"expected a contiguous float64 array of {n} elements")
+            else:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                if a.size != n:
+                    raise ValueError(f"expected {n} elements, got {a.size}")
+            self.obj, self.ptr = a, a.ctypes.data
+
+
+class Lattice:
+    """One context: B >= 1 independent lattices advanced by the CUDA library.
+
+    lengths: int or sequence of ints (>= 3). s_e: the free rate (scalar or per lattice).
+    s_psi / s_eps: <= 0 selects the paper's coupling / 1.5. bc: 0 periodic, 1 bounce-back
+    (scalar or per lattice). precision: "f64" or "f32" (FP32 shifted populations).
+    s0: per-lattice reference entropy (None: phys["s0"]). phys: dict of lbm_phys fields.
+    """
+
+    def __init__(self, lengths, lam: float = 1.0, s_e=1.5, s_psi=0.0, s_eps=0.0, bc=0,
+                 precision: str = "f64", phys: dict | None = None, s0=None, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        install_torch_allocator()
+        lengths = np.atleast_1d(np.asarray(lengths, dtype=np.int64))
+        B = lengths.size
+        s_e = np.broadcast_to(np.asarray(s_e, dtype=np.float64), (B,))
+        s_psi = np.broadcast_to(np.asarray(s_psi, dtype=np.float64), (B,))
+        s_eps = np.broadcast_to(np.asarray(s_eps, dtype=np.float64), (B,))
+        bcs = np.ascontiguousarray(np.broadcast_to(np.asarray(bc, dtype=np.int32), (B,)))
+        rates = (lbm_rates * B)(*[lbm_rates(float(a), float(b), float(c)) for a, b, c in zip(s_e, s_psi, s_eps)])
+        ph = None
+        if phys is not None:
+            base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, source_on=1, reserved=0)
+            base.update(phys)
+            ph = lbm_phys(**base)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.precision = PRECISIONS[precision]
+        self.lengths = lengths
+        self.B = B
+        ctx = ctypes.c_void_p()
+        s0_arr = None if s0 is None else np.ascontiguousarray(np.broadcast_to(np.asarray(s0, dtype=np.float64), (B,)))
+        rc = self.lib.lbm_create_batch(
+            ctypes.byref(ctx), B, lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(lam), rates,
+            bcs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            None if s0_arr is None else s0_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            self.precision, None if ph is None else ctypes.byref(ph), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_create_batch failed")
+        self.ctx = ctx
+        self.N = int(self.lib.lbm_total_nodes(ctx))
+        self.offsets = np.r_[0, np.cumsum(lengths)]
+
+    # -- helpers ---------------------------------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != LBM_OK:
+            raise LbmError(rc, f"{what}: {self.lib.lbm_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI mirrors ---------------------------------------------------------------------------
+    def set_state(self, rho, u, p):
+        a, b, c = (_Arr(x, self.N) for x in (rho, u, p))
+        self._check(self.lib.lbm_set_state(self.ctx, a.ptr, b.ptr, c.ptr), "lbm_set_state")
+
+    def set_state_entropy(self, rho, u, s):
+        a, b, c = (_Arr(x, self.N) for x in (rho, u, s))
+        self._check(self.lib.lbm_set_state_entropy(self.ctx, a.ptr, b.ptr, c.ptr), "lbm_set_state_entropy")
+
+    def step(self, nsteps: int):
+        self._check(self.lib.lbm_step(self.ctx, int(nsteps)), "lbm_step")
+
+    def moments(self, out=None, device: bool = True):
+        """(rho, J, zeta, e, psi, eps) as six float64 arrays: torch tensors on the GPU (device=True)
+        or numpy arrays (device=False). ``out`` may give six preallocated arrays (or None)."""
+        torch = _torch()
+        if out is None:
+            if device:
+                out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(6)]
+            else:
+                out = [np.empty(self.N) for _ in range(6)]
+        arrs = [None if o is None else _Arr(o, self.N, writable=True) for o in out]
+        ptrs = [None if a is None else a.ptr for a in arrs]
+        self._check(self.lib.lbm_moments(self.ctx, *ptrs), "lbm_moments")
+        return out
+
+    def populations(self, device: bool = False):
+        torch = _torch()
+        out = torch.empty(6 * self.N, dtype=torch.float64, device="cuda") if device else np.empty(6 * self.N)
+        a = _Arr(out, 6 * self.N, writable=True)
+        self._check(self.lib.lbm_get_populations(self.ctx, a.ptr), "lbm_get_populations")
+        return out.reshape(6, self.N)
+
+    def set_populations(self, fd):
+        a = _Arr(fd.reshape(-1) if hasattr(fd, "reshape") else fd, 6 * self.N)
+        self._check(self.lib.lbm_set_populations(self.ctx, a.ptr), "lbm_set_populations")
+
+    def diagnostics(self, raise_unstable: bool = False):
+        """(sums [B, 4] = (sum rho, sum J, sum zeta, sum rho E), flags [B], status)."""
+        sums = np.zeros((self.B, 4))
+        flags = np.zeros(self.B, dtype=np.int32)
+        rc = self.lib.lbm_diagnostics(self.ctx, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if rc not in (LBM_OK, LBM_ERR_UNSTABLE) or (raise_unstable and rc != LBM_OK):
+            self._check(rc, "lbm_diagnostics")
+        return sums, flags, rc
+
+    def set_config(self, steps_per_launch: int = 0, block_threads: int = 0):
+        self._check(self.lib.lbm_set_config(self.ctx, int(steps_per_launch), int(block_threads)), "lbm_set_config")
+
+    def get_config(self):
+        k, nt = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm_get_config(self.ctx, ctypes.byref(k), ctypes.byref(nt)), "lbm_get_config")
+        return k.value, nt.value
+
+    def autotune(self, trials: int = 3):
+        self._check(self.lib.lbm_autotune(self.ctx, int(trials)), "lbm_autotune")
+        return self.get_config()
+
+    def save(self, path: str):
+        self._check(self.lib.lbm_save(self.ctx, path.encode()), "lbm_save")
+
+    def load(self, path: str):
+        self._check(self.lib.lbm_load(self.ctx, path.encode()), "lbm_load")
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbm_steps_done(self.ctx))

@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/*.h declares.
+No compute call is made (no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1802_02369_gb300 import build
+
+    return build.build()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names - {"lbm_alloc_fn", "lbm_free_fn"})
+
+
+def test_library_exports_every_declared_function(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_declares_the_same_functions(lib_path):
+    from paper_1802_02369_gb300 import lbm
+
+    lib = lbm.load_library(lib_path)
+    assert lbm.header_functions() == _declared()
+    for n in _declared():
+        assert getattr(lib, n).argtypes is not None or n in ("lbm_destroy",)
+
+
+def test_invalid_arguments_are_rejected_without_gpu(lib_path):
+    """Argument validation happens before any CUDA call."""
+    from paper_1802_02369_gb300 import lbm
+
+    lib = lbm.load_library(lib_path)
+    ctx = ctypes.c_void_p()
+    r = lbm.lbm_rates(1.5, 0.0, 0.0)
+    assert lib.lbm_create(ctypes.byref(ctx), 2, 1.0, ctypes.byref(r), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_create(ctypes.byref(ctx), 64, 0.0, ctypes.byref(r), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(r), 7, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(r), 0, 5, None, None) == lbm.LBM_ERR_INVALID_ARG
+    bad = lbm.lbm_rates(2.0, 0.0, 0.0)
+    assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(bad), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    bad = lbm.lbm_rates(1.5, 2.5, 0.0)
+    assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(bad), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_total_nodes(None) == -1

@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances: a field value a (GPU) and b (oracle) agree when |a - b| <= tol * max(|b|, S), with S
+the natural scale of that moment in lattice units (rho0, rho0 lambda, rho0 c_p, rho0 lambda^2,
+rho0 c_p lambda, rho0 c_p lambda^2 for rho, J, zeta, e, psi, eps). tol = 1e-12 for FP64 and 1e-5
+for FP32 on smooth waves; on shocks FP32 is held to L1(rho) = mean |rho_a - rho_b| / rho0 <= 1e-4.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1802_02369_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_02369_gb300 import build, lbm as L
+
+    build.build()
+    return L
+
+
+def scales(lam=1.0, cp=1.0, rho0=1.0):
+    return np.array([rho0, rho0 * lam, rho0 * cp, rho0 * lam ** 2, rho0 * cp * lam, rho0 * cp * lam ** 2])
+
+
+def rel_err(gpu_m, ora_m, sc):
+    """gpu_m: six arrays; ora_m: [N, 6] oracle moments. Max normalised error per field."""
+    g = np.stack([np.asarray(x) for x in gpu_m], axis=1)
+    den = np.maximum(np.abs(ora_m), sc[None, :])
+    return (np.abs(g - ora_m) / den).max(axis=0)
+
+
+def gpu_run(L, rho, u, p, nsteps, s_e, bc=0, precision="f64", lam=1.0, config=None, phys=None):
+    lat = L.Lattice(rho.size, lam=lam, s_e=s_e, bc=bc, precision=precision, phys=phys)
+    if config:
+        lat.set_config(*config)
+    lat.set_state(rho, u, p)
+    lat.step(nsteps)
+    m = lat.moments(device=False)
+    lat.close()
+    return m
+
+
+def oracle_run(O, rho, u, p, nsteps, s_e, bc=0, lam=1.0, **kw):
+    ph = O.default_phys(lam=lam, bc=bc, **kw)
+    fd = O.run(ph, O.coupled_rates(s_e, ph.gamma, ph.Pr), O.init(ph, rho, u, p=p), nsteps, NTHREADS)
+    return O.moments(ph, fd)
+
+
+def smooth_data(N, seed, amp=0.03, bc=0, p_ref=0.25 / 1.4):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * np.arange(N) / N
+    rho = 1.0 + sum(amp * rng.uniform(-1, 1) * np.sin(k * x + rng.uniform(0, 6.3)) for k in (1, 2, 3))
+    u = sum(amp * rng.uniform(-1, 1) * np.sin(k * x + rng.uniform(0, 6.3)) for k in (1, 2))
+    if bc:
+        u = u * np.sin(np.pi * (np.arange(N) + 0.5) / N)
+    p = p_ref * rho ** 1.4 * (1.0 + sum(amp * rng.uniform(-1, 1) * np.cos(k * x) for k in (1, 2)))
+    return rho, u, p
+
+
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s_e,nsteps", [(1.0, 500), (1.2, 500), (1.5, 100)])
+def test_sod_fp64(O, lbm, s_e, nsteps):
+    """Sod data (pressures in units of p0), N = 256, periodic, FP64."""
+    ph = O.default_phys()
+    rho, u, p = W.sod(256, ph.p0)
+    err = rel_err(gpu_run(lbm, rho, u, p, nsteps, s_e), oracle_run(O, rho, u, p, nsteps, s_e), scales())
+    assert err.max() <= 1e-12, err
+
+
+@pytest.mark.parametrize("N", [3, 4, 5, 7, 64, 1000, 4099])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_small_and_ragged_sizes_fp64(O, lbm, N, bc):
+    rho, u, p = smooth_data(N, seed=N + 7 * bc, bc=bc)
+    ref = oracle_run(O, rho, u, p, 200, 1.3, bc=bc)
+    outs = []
+    for cfg in [(1, 256), (2, 512), (4, 1024), (8, 256)]:
+        g = gpu_run(lbm, rho, u, p, 200, 1.3, bc=bc, config=cfg)
+        assert rel_err(g, ref, scales()).max() <= 1e-12, cfg
+        outs.append(np.stack(g))
+    for o in outs[1:]:  # identical arithmetic per node: bitwise equal across tilings and depths
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_steepening_wave_multi_tile(O, lbm, precision, tol):
+    """The 1000-step steepening wave (rho = 1 + 0.1 sin, u = 0.1 sin, adiabatic, s_e = 1.2) on a
+    lattice of many tiles with a ragged last tile."""
+    ph = O.default_phys()
+    N = (1 << 16) + 123
+    rho, u, p = W.steepening_wave(N, 0.1, ph.p0)
+    ref = oracle_run(O, rho, u, p, 1000, 1.2)
+    err = rel_err(gpu_run(lbm, rho, u, p, 1000, 1.2, precision=precision), ref, scales())
+    assert err.max() <= tol, err
+
+
+def test_shocks_fp32_l1(O, lbm):
+    """Shock cases in FP32: the section 9 strong wave (delta = 0.1, N = 160, T_max = 3, s_e = 1.9)
+    and Sod (s_e = 1.2, 500 steps): L1(rho) <= 1e-4."""
+    ph = O.default_phys()
+    cases = [(W.progressive_wave(160, 0.1, 0.5, ph.p0), 480, 1.9), (W.sod(256, ph.p0), 500, 1.2)]
+    for (rho, u, p), n, s_e in cases:
+        ref = oracle_run(O, rho, u, p, n, s_e)
+        g = gpu_run(lbm, rho, u, p, n, s_e, precision="f32")
+        assert np.mean(np.abs(np.asarray(g[0]) - ref[:, 0])) <= 1e-4
+
+
+def test_batched_ragged_fp64(O, lbm):
+    """Independent lattices of uneven lengths, rates and boundaries in one context."""
+    rng = np.random.default_rng(1802)
+    B = 23
+    lengths = rng.integers(3, 5000, B)
+    lengths[:3] = [3, 4, 2049]
+    s_e = rng.uniform(1.0, 1.9, B)
+    bc = rng.integers(0, 2, B)
+    data = [smooth_data(int(n), seed=100 + b, amp=0.02, bc=int(bc[b])) for b, n in enumerate(lengths)]
+    lat = lbm.Lattice(lengths, s_e=s_e, bc=bc)
+    lat.set_state(*[np.concatenate([d[k] for d in data]) for k in range(3)])
+    lat.step(300)
+    g = np.stack(lat.moments(device=False), axis=1)
+    sums, flags, rc = lat.diagnostics()
+    lat.close()
+    off = np.r_[0, np.cumsum(lengths)]
+    for b in range(B):
+        ref = oracle_run(O, *data[b], 300, s_e[b], bc=int(bc[b]))
+        gb = g[off[b]:off[b + 1]]
+        assert rel_err(list(gb.T), ref, scales()).max() <= 1e-12, b
+        ph = O.default_phys(bc=int(bc[b]))
+        osum, oflag = O.diagnostics(ph, O.run(ph, O.coupled_rates(s_e[b]), O.init(ph, *data[b][:2], p=data[b][2]), 300))
+        np.testing.assert_allclose(sums[b], osum, rtol=1e-12, atol=1e-12 * lengths[b])
+        assert flags[b] == oflag == 0
+    assert rc == lbm.LBM_OK
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_full_size_sampled_windows(O, lbm, precision):
+    """The benchmark workload at full size (N = 2^26, steepening wave, s_e = 1.2, 1000 steps, the
+    default autotuned launch configuration) checked on sampled nodes: after T steps a node depends
+    only on the initial data within 2T nodes, so the oracle run on a periodic window of 4T + 64
+    nodes reproduces the 64 central nodes exactly."""
+    import torch
+
+    ph = O.default_phys()
+    N, T = 1 << 26, 1000
+    rho, u, p = W.steepening_wave(N, 0.1, ph.p0)
+    lat = lbm.Lattice(N, s_e=1.2, precision=precision)
+    lat.set_state(rho, u, p)
+    lat.autotune(1)
+    lat.set_state(rho, u, p)
+    lat.step(T)
+    g = [x.cpu().numpy() for x in lat.moments(device=True)]
+    lat.close()
+    torch.cuda.empty_cache()
+    tol = 1e-12 if precision == "f64" else 1e-5
+    r = O.coupled_rates(1.2)
+    for c in (0, 1, N // 3, N // 2 + 5, N - 33):
+        idx = (np.arange(c - 2 * T - 32, c + 2 * T + 32)) % N
+        fd = O.run(ph, r, O.init(ph, rho[idx], u[idx], p=p[idx]), T, NTHREADS)
+        ref = O.moments(ph, fd)[2 * T:2 * T + 64]
+        got = [x[idx[2 * T:2 * T + 64]] for x in g]
+        assert rel_err(got, ref, scales()).max() <= tol, c
+
+
+def test_diagnostics_and_conservation(O, lbm):
+    ph = O.default_phys()
+    rho, u, p = smooth_data(3000, seed=5, amp=0.05)
+    lat = lbm.Lattice(3000, s_e=1.4)
+    lat.set_state(rho, u, p)
+    s0, f0, _ = lat.diagnostics()
+    osum, _ = O.diagnostics(ph, O.init(ph, rho, u, p=p))
+    np.testing.assert_allclose(s0[0], osum, rtol=1e-13, atol=1e-12)
+    prev = s0[0, 2]
+    for _ in range(20):
+        lat.step(50)
+        s, f, rc = lat.diagnostics()
+        assert rc == 0 and f[0] == 0
+        assert abs(s[0, 0] - s0[0, 0]) <= 1e-13 * s0[0, 0]
+        assert abs(s[0, 1] - s0[0, 1]) <= 1e-13 * s0[0, 0]
+        assert s[0, 2] >= prev - 1e-15 * s0[0, 0]
+        prev = s[0, 2]
+    lat.close()
+
+
+def test_unstable_literal_sod_is_flagged(O, lbm):
+    """Literal Sod pressures (c^2 = 1.4 lambda^2 > lambda^2) blow up; diagnostics say so."""
+    rho, u, p = W.sod(256, 1.0)
+    lat = lbm.Lattice(256, s_e=1.5)
+    lat.set_state(rho, u, p)
+    lat.step(10)
+    sums, flags, rc = lat.diagnostics()
+    lat.close()
+    ph = O.default_phys()
+    _, oflag = O.diagnostics(ph, O.run(ph, O.coupled_rates(1.5), O.init(ph, rho, u, p=p), 10))
+    assert rc == lbm.LBM_ERR_UNSTABLE and flags[0] != 0 and oflag != 0
+
+
+def test_host_and_device_inputs_agree(lbm):
+    import torch
+
+    rho, u, p = smooth_data(777, seed=3)
+    a = lbm.Lattice(777, s_e=1.3)
+    a.set_state(rho, u, p)
+    b = lbm.Lattice(777, s_e=1.3)
+    b.set_state(*[torch.from_numpy(x).cuda() for x in (rho, u, p)])
+    for lat in (a, b):
+        lat.step(37)
+    pa, pb = a.populations(), b.populations(device=True).cpu().numpy()
+    assert np.array_equal(pa, pb)
+    ma = a.moments(device=False)
+    mb = [x.cpu().numpy() for x in a.moments(device=True)]
+    for x, y in zip(ma, mb):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_checkpoint_resume_is_bitwise(lbm, tmp_path, precision):
+    rho, u, p = smooth_data(5000, seed=9, amp=0.05)
+    a = lbm.Lattice(5000, s_e=1.6, precision=precision)
+    a.set_state(rho, u, p)
+    a.step(100)
+    path = str(tmp_path / "ckpt.bin")
+    a.save(path)
+    a.step(150)
+    b = lbm.Lattice(5000, s_e=1.6, precision=precision)
+    b.load(path)
+    assert b.steps_done == 100
+    b.step(150)
+    assert np.array_equal(a.populations(), b.populations())
+    c = lbm.Lattice(5000, s_e=1.7, precision=precision)   # mismatched parameters are refused
+    with pytest.raises(lbm.LbmError):
+        c.load(path)
+    for x in (a, b, c):
+        x.close()
+
+
+def test_populations_roundtrip_and_autotune_keeps_result(O, lbm):
+    rho, u, p = smooth_data(3333, seed=4)
+    ph = O.default_phys()
+    fd = O.init(ph, rho, u, p=p)
+    lat = lbm.Lattice(3333, s_e=1.25)
+    lat.set_populations(np.ascontiguousarray(fd.T))
+    np.testing.assert_allclose(lat.populations(), fd.T, rtol=0, atol=1e-16)
+    lat.autotune(1)
+    lat.step(64)
+    ref = O.moments(ph, O.run(ph, O.coupled_rates(1.25), fd, 64))
+    assert rel_err(lat.moments(device=False), ref, scales()).max() <= 1e-12
+    lat.close()
