@@ -198,22 +198,28 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     torch.cuda.set_device(local)
     build.build()
     hbm_peak, peak_kind = measured_peaks()
-    rho, u, p = workload_fields(N_NODES)
+    NN = args.nodes
+    rho, u, p = workload_fields(NN)
     d_rho, d_u, d_p = (torch.from_numpy(x).cuda() for x in (rho, u, p))
     results = {}
+    precs = args.precisions.split(",")
     with ClockSampler(local) as clk:
-        for prec in ("f32", "f64"):
-            lat = lbm.Lattice(N_NODES, s_e=S_E, precision=prec)
+        for prec in precs:
+            lat = lbm.Lattice(NN, s_e=S_E, precision=prec)
             lat.set_state(d_rho, d_u, d_p)
-            k, nt = lat.autotune(2)
+            if args.config:
+                lat.set_config(*[int(x) for x in args.config.split(",")])
+                k, nt = lat.get_config()
+            else:
+                k, nt = lat.autotune(2)
             lat.set_state(d_rho, d_u, d_p)
             steps = args.steps if prec == "f32" else max(8, min(args.steps, 200))
             steps = ((steps + k - 1) // k) * k
             ms = time_device(lat, torch, steps, max(args.warmup, 3) * k, dist, world)
             launches = steps // k
-            glups = world * N_NODES * steps / (ms * 1e-3) / 1e9
+            glups = world * NN * steps / (ms * 1e-3) / 1e9
             launch_ms = ms / launches
-            alg_bytes = N_NODES * BYTES_PER_NODE[prec]          # one read + one write of the state
+            alg_bytes = NN * BYTES_PER_NODE[prec]               # one read + one write of the state
             achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
             sums, flags, rc = lat.diagnostics()
             results[prec] = dict(value=glups, ms_per_step=ms / steps, steps=steps, k=k, block_threads=nt,
@@ -222,6 +228,10 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             lat.close()
             torch.cuda.empty_cache()
     clocks = clk.summary()
+    if NN != N_NODES or len(precs) != 2:
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "nodes": NN, "results": results, "clocks": clocks}), flush=True)
+        return
 
     # End to end through the C-ABI with pinned host buffers: state in, K steps, (rho, J, zeta) out.
     r32 = results["f32"]
@@ -293,6 +303,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # Profiling of smaller cases (not the benchmark line): lattice size, precisions, fixed config.
+    ap.add_argument("--nodes", type=int, default=N_NODES)
+    ap.add_argument("--precisions", default="f32,f64")
+    ap.add_argument("--config", default="", help="k,block_threads instead of autotuning")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
