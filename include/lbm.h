@@ -43,6 +43,7 @@ extern "C" {
 #define LBM_ERR_UNSTABLE (-4)    /* diagnostics found a non-finite value, rho <= 0 or T <= 0 */
 #define LBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired */
 #define LBM_ERR_IO (-6)          /* checkpoint file could not be written or read, or mismatched */
+#define LBM_ERR_TOO_LARGE (-7)   /* input larger than a fixed-size scratch area allows */
 
 /* Boundary conditions (per lattice). Periodic is the paper's (section 9). Bounce-back is not in
  * the paper: halfway bounce-back at both ends, f+(0) <- f-*(0), f-(N-1) <- f+*(N-1) (same for g),
@@ -144,6 +145,24 @@ int lbm_autotune(lbm_ctx *ctx, int32_t trials);
  * bitwise identical to an uninterrupted one. Synchronises. */
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Diagnostics that allocate no device memory. The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc (code inside host callbacks or another framework's memory pool, or a
+ * process whose device memory is all handed to its own allocator). It computes, for ONE lattice,
+ * the same FP64 sums as lbm_diagnostics (sum rho, sum J, sum zeta, sum of p/(gamma-1) + rho u^2/2)
+ * and the same flag bits, from populations the caller holds.
+ *  fd: DEVICE pointer to float64 populations, plane-major [6][N] in the order (f0, f+, f-, g0, g+, g-)
+ *      (the layout lbm_get_populations writes). N >= 1 and N <= 2^26 (else LBM_ERR_TOO_LARGE).
+ *  lambda, phys: as for lbm_create (phys NULL = section 9 defaults; phys->s0 is the entropy reference).
+ *  sums[4], flags[1]: both host or both device pointers. Host outputs: the call synchronises `stream`
+ *      and returns LBM_ERR_UNSTABLE if a flag is set. Device outputs: the call only enqueues work.
+ *  stream: cudaStream_t or NULL.
+ * The reduction scratch is a file-scope __device__ array of about 300 KB that every GPU loading the
+ * library holds until exit; its address is looked up once per device on the first call with that
+ * device current, so make the first call on each device before any stream capture. Every call
+ * shares the array: calls whose kernels overlap on the GPU race (issue them on one stream). */
+int lbm_diagnostics_noalloc(const double *fd, int64_t N, double lambda, const lbm_phys *phys, double *sums,
+                            int32_t *flags, void *stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ LBM_ERR_OOM = -3
 LBM_ERR_UNSTABLE = -4
 LBM_ERR_TIMEOUT = -5
 LBM_ERR_IO = -6
+LBM_ERR_TOO_LARGE = -7
 LBM_BC_PERIODIC = 0
 LBM_BC_BOUNCEBACK = 1
 LBM_F64 = 0
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH):
             "lbm_autotune": (i32, [vp, i32]),
             "lbm_save": (i32, [vp, ctypes.c_char_p]),
             "lbm_load": (i32, [vp, ctypes.c_char_p]),
+            "lbm_diagnostics_noalloc": (i32, [vp, i64, d, P(lbm_phys), vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -136,6 +138,22 @@ def install_torch_allocator():
     rc = lib.lbm_set_allocator(a, f, None)
     if rc != LBM_OK:
         raise LbmError(rc, "lbm_set_allocator failed")
+
+
+def diagnostics_noalloc(fd, N: int, lam: float = 1.0, phys=None, sums=None, flags=None, stream=None) -> int:
+    """lbm_diagnostics_noalloc: FP64 sums of one lattice from device populations fd ([6, N] float64
+    torch tensor on the GPU) without any device allocation. sums/flags: numpy (host) or torch
+    (device) outputs of 4 float64 / 1 int32. Returns the status code."""
+    lib = load_library()
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ph = None if phys is None else ctypes.byref(phys)
+
+    def ptr(x):
+        return x.data_ptr() if isinstance(x, torch.Tensor) else x.ctypes.data
+
+    return lib.lbm_diagnostics_noalloc(ptr(fd), int(N), float(lam), ph, ptr(sums), ptr(flags),
+                                       ctypes.c_void_p(st.cuda_stream))
 
 
 class _Arr:
