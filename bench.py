@@ -209,9 +209,9 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             lat.set_state(d_rho, d_u, d_p)
             if args.config:
                 lat.set_config(*[int(x) for x in args.config.split(",")])
-                k, nt = lat.get_config()
+                k, nt, vpt = lat.get_config()
             else:
-                k, nt = lat.autotune(2)
+                k, nt, vpt = lat.autotune(2)
             lat.set_state(d_rho, d_u, d_p)
             steps = args.steps if prec == "f32" else max(8, min(args.steps, 200))
             steps = ((steps + k - 1) // k) * k
@@ -222,7 +222,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             alg_bytes = NN * BYTES_PER_NODE[prec]               # one read + one write of the state
             achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
             sums, flags, rc = lat.diagnostics()
-            results[prec] = dict(value=glups, ms_per_step=ms / steps, steps=steps, k=k, block_threads=nt,
+            results[prec] = dict(value=glups, ms_per_step=ms / steps, steps=steps, k=k, block_threads=nt, nodes_per_thread=vpt,
                                  launches=launches, launch_ms=launch_ms, achieved=achieved,
                                  effective_gbs=glups / world * BYTES_PER_NODE[prec], flags=int(flags[0]))
             lat.close()
@@ -239,7 +239,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     h = [torch.from_numpy(x).pin_memory() for x in (rho, u, p)]
     outs = [torch.empty(N_NODES, dtype=torch.float64).pin_memory() for _ in range(3)]
     lat = lbm.Lattice(N_NODES, s_e=S_E, precision="f32")
-    lat.set_config(r32["k"], r32["block_threads"])
+    lat.set_config(r32["k"], r32["block_threads"], r32["nodes_per_thread"])
     lat.set_state(*h)
     lat.step(r32["k"] * 3)
     lat.moments(out=outs + [None, None, None])
@@ -286,6 +286,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_NODES, "precision": "f32 shifted populations",
                        "steps_per_launch": f32["k"], "block_threads": f32["block_threads"],
+                       "nodes_per_thread": f32["nodes_per_thread"],
                        "l2": "inputs larger than L2 (FP32 state 1.6 GB, FP64 3.2 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof(f32, "f32"),
@@ -306,7 +307,7 @@ def main():
     # Profiling of smaller cases (not the benchmark line): lattice size, precisions, fixed config.
     ap.add_argument("--nodes", type=int, default=N_NODES)
     ap.add_argument("--precisions", default="f32,f64")
-    ap.add_argument("--config", default="", help="k,block_threads instead of autotuning")
+    ap.add_argument("--config", default="", help="k,block_threads,nodes_per_thread instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

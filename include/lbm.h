@@ -130,14 +130,37 @@ int lbm_set_populations(lbm_ctx *ctx, const double *fd);
 int lbm_diagnostics(lbm_ctx *ctx, double *sums, int32_t *flags);
 
 /* Kernel configuration: steps_per_launch k in {1, 2, 4, 8} (temporal blocking: k steps per HBM
- * round trip, 2k halo nodes per tile side) and block_threads in {256, 512, 1024} (tile width).
- * 0 keeps the current value. */
-int lbm_set_config(lbm_ctx *ctx, int32_t steps_per_launch, int32_t block_threads);
-int lbm_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch, int32_t *block_threads);
+ * round trip, 2k halo nodes recomputed on each tile side), block_threads in {128, 256, 512, 1024}
+ * and nodes_per_thread in {1, 2, 4} (tile width block_threads * nodes_per_thread; 1024 x 4 is not
+ * supported; the tile must keep at least 32 interior nodes). 0 keeps the current value. */
+int lbm_set_config(lbm_ctx *ctx, int32_t steps_per_launch, int32_t block_threads, int32_t nodes_per_thread);
+int lbm_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch, int32_t *block_threads,
+                   int32_t *nodes_per_thread);
 
-/* Times every (k, block_threads) pair on the current state (which is left unchanged; each trial
- * writes only the second buffer) and keeps the fastest per node-update. trials >= 1 timed
- * launches per candidate. Synchronises. Needs a state. */
+/* Execution mode of lbm_step.
+ * LBM_MODE_LAUNCH: one kernel launch per k steps (default).
+ * LBM_MODE_PERSISTENT: all whole blocks of k steps in ONE persistent launch; CTAs claim (block, tile)
+ *   work units in order and a unit waits only for the neighbouring tiles of its lattice to finish the
+ *   previous block (bounded spin; see lbm_status). Results are bitwise equal to LBM_MODE_LAUNCH.
+ * LBM_MODE_PERSISTENT_GRAPH: the same launch (with its counter resets) captured once in a CUDA graph
+ *   per (number of blocks, buffer parity, configuration) and replayed.
+ * A remainder of nsteps not divisible by k runs as ordinary launches. */
+enum { LBM_MODE_LAUNCH = 0, LBM_MODE_PERSISTENT = 1, LBM_MODE_PERSISTENT_GRAPH = 2 };
+int lbm_set_mode(lbm_ctx *ctx, int32_t mode);
+
+/* Synchronises the stream and reports whether a bounded device-side wait of a persistent launch
+ * expired since the last call: LBM_ERR_TIMEOUT (the state is then not a valid time step; set it
+ * again) or LBM_OK. Clears the status word. */
+int lbm_status(lbm_ctx *ctx);
+
+/* Failure-detection test hook for persistent launches: spin_limit >= 1 polls (about 100 ns apart)
+ * before a wait gives up (default 2e7), and withhold_tile >= 0 names a tile whose first time block
+ * is computed but never released, so that its neighbours' waits must expire (-1: none). */
+int lbm_debug_persistent(lbm_ctx *ctx, int64_t spin_limit, int64_t withhold_tile);
+
+/* Times every valid (k, block_threads, nodes_per_thread) on the current state (which is left
+ * unchanged; each trial writes only the second buffer, over at most 16384 tiles) and keeps the
+ * fastest per node-update. trials >= 1 timed launches per candidate. Synchronises. Needs a state. */
 int lbm_autotune(lbm_ctx *ctx, int32_t trials);
 
 /* Checkpoint: writes / reads the populations, step counter and parameters to a host file. A load
@@ -145,6 +168,29 @@ int lbm_autotune(lbm_ctx *ctx, int32_t trials);
  * bitwise identical to an uninterrupted one. Synchronises. */
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Reverse mode (adjoint) of T time steps, with sqrt(T) checkpointing: the forward run keeps
+ * ceil(T / S) checkpoints (S = round(sqrt(T))) and the backward sweep recomputes each segment's S
+ * states before stepping the adjoint back through them. Device memory: about ceil(T/S) + S + 1
+ * copies of the state, released by lbm_adjoint_release (or lbm_destroy).
+ *
+ * lbm_adjoint_forward: runs T >= 1 steps from the current state (which must have been set by
+ *   lbm_set_state or lbm_set_state_entropy for the rho/u gradients below to be meaningful; the
+ *   population gradient is exact for any state) and leaves the state at time T.
+ * lbm_adjoint_backward: given dL/drho(T) per node (float64, host or device), returns
+ *   dL/drho(0) and dL/du(0) per node at fixed initial specific entropy (through the equilibrium
+ *   initialisation), dL/ds_e and dL/ds_psi per lattice in dL_drates[2 b + 0/1] (s_e and s_psi
+ *   taken as independent; nu and kappa of the source follow s_e as in eq. (nu-d1q3q3)), and
+ *   optionally dL/df(0) as float64 plane-major [6][N]. Outputs may be NULL, host or device.
+ *   Rate gradients are accumulated in FP64 in a fixed order. Synchronises.
+ * lbm_adjoint: forward T steps, loss = sum over all nodes of (rho(T) - rho_target)^2 (FP64,
+ *   fixed-order reduction) into *loss, then the backward sweep. */
+int lbm_adjoint_forward(lbm_ctx *ctx, int64_t T);
+int lbm_adjoint_backward(lbm_ctx *ctx, const double *dL_drho_T, double *dL_drho0, double *dL_du0,
+                         double *dL_drates, double *dL_dfd0);
+int lbm_adjoint(lbm_ctx *ctx, int64_t T, const double *rho_target, double *loss, double *dL_drho0,
+                double *dL_du0, double *dL_drates);
+int lbm_adjoint_release(lbm_ctx *ctx);
 
 /* Diagnostics that allocate no device memory. The paper has no counterpart: this exists for callers
  * that cannot call cudaMalloc (code inside host callbacks or another framework's memory pool, or a

@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,33 +36,57 @@ struct PhysD {
   double wf1() const { return p0 / (2.0 * rho0 * lam * lam); }
 };
 
-template <typename R>
-Consts<R> make_consts(const PhysD& p) {
-  Consts<R> c;
+template <typename X>
+X lift(double v) {
+  if constexpr (std::is_same<X, float2>::value) return make_float2((float)v, (float)v);
+  else return X(v);
+}
+
+template <typename X>
+Consts<X> make_consts(const PhysD& p) {
+  Consts<X> c;
   const double l = p.lam, l2 = l * l, af = p.rho0, ag = p.rho0 * p.cp;
-  c.rho0 = R(p.rho0);
-  c.lam = R(l);
-  c.two_lam2 = R(2.0 * l2);
-  c.inv_af = R(1.0 / af);
-  c.inv_af_l = R(1.0 / (af * l));
-  c.inv_af_l2 = R(1.0 / (af * l2));
-  c.af_l = R(af * l);
-  c.af_l2 = R(af * l2);
-  c.ag = R(ag);
-  c.ag_l = R(ag * l);
-  c.ag_l2 = R(ag * l2);
-  c.inv_ag = R(1.0 / ag);
-  c.inv_ag_l = R(1.0 / (ag * l));
-  c.inv_ag_l2 = R(1.0 / (ag * l2));
-  c.gamma = R(p.gamma);
-  c.inv_cp = R(1.0 / p.cp);
-  c.p0 = R(p.p0);
-  c.inv_r = R(1.0 / p.r());
-  c.e_r = R(p.e_r());
-  c.cp_log = R((1.0 - 1.0 / p.gamma) * p.cp);
-  c.cp_over_Pr = R(p.cp / p.Pr);
+  c.rho0 = lift<X>(p.rho0);
+  c.lam = lift<X>(l);
+  c.two_lam2 = lift<X>(2.0 * l2);
+  c.m_two_lam2 = lift<X>(-2.0 * l2);
+  c.inv_af = lift<X>(1.0 / af);
+  c.inv_af_l = lift<X>(1.0 / (af * l));
+  c.inv_af_l2 = lift<X>(1.0 / (af * l2));
+  c.af_l = lift<X>(af * l);
+  c.af_l2 = lift<X>(af * l2);
+  c.ag = lift<X>(ag);
+  c.ag_l = lift<X>(ag * l);
+  c.ag_l2 = lift<X>(ag * l2);
+  c.inv_ag = lift<X>(1.0 / ag);
+  c.inv_ag_l = lift<X>(1.0 / (ag * l));
+  c.inv_ag_l2 = lift<X>(1.0 / (ag * l2));
+  c.gamma = lift<X>(p.gamma);
+  c.inv_cp = lift<X>(1.0 / p.cp);
+  c.p0 = lift<X>(p.p0);
+  c.inv_r = lift<X>(1.0 / p.r());
+  c.e_r = lift<X>(p.e_r());
+  c.cp_log = lift<X>((1.0 - 1.0 / p.gamma) * p.cp);
+  c.cp_over_Pr = lift<X>(p.cp / p.Pr);
+  c.one = lift<X>(1.0);
+  c.m_one = lift<X>(-1.0);
+  c.two = lift<X>(2.0);
+  c.m_two = lift<X>(-2.0);
+  c.three = lift<X>(3.0);
+  c.half = lift<X>(0.5);
+  c.m_half = lift<X>(-0.5);
+  c.third = lift<X>(1.0 / 3.0);
+  c.sixth = lift<X>(1.0 / 6.0);
   c.source_on = p.source_on;
   return c;
+}
+
+template <typename R>
+lbm::ConstSet<R> make_constset(const PhysD& p) {
+  lbm::ConstSet<R> k;
+  k.s = make_consts<R>(p);
+  k.p = make_consts<float2>(p);
+  return k;
 }
 
 void* dev_alloc(size_t bytes, cudaStream_t st) {
@@ -306,7 +332,7 @@ struct lbm_ctx {
   int cur = 0;
   bool has_state = false;
   long long ntiles = 0;
-  int K = 1, NT = 512;
+  int K = 1, NT = 512, V = 1;
   long long nchunks = 0;
   double* d_part = nullptr;
   int* d_pflag = nullptr;
@@ -316,6 +342,26 @@ struct lbm_ctx {
   size_t stage_bytes = 0;
   long long steps_done = 0;
   std::string err;
+  // Persistent execution (lbm_set_mode).
+  int mode = LBM_MODE_LAUNCH;
+  int* d_done = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int* d_status = nullptr;
+  long long spin_limit = 20000000;  // about 2 s of polling per wait
+  long long withhold = -1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_key[6] = {-1, -1, -1, -1, -1, -1};
+  // Adjoint (lbm_adjoint_forward / lbm_adjoint_backward).
+  long long adj_T = -1, adj_seg = 0, adj_nseg = 0;
+  std::vector<void*> ckpt, stash;
+  void* adj_a[2] = {nullptr, nullptr};
+  LatDev* d_lat_adj = nullptr;
+  long long adj_ntiles = 0;
+  double* d_gtile = nullptr;
+  double* d_rgrad = nullptr;
+  double* d_lpart = nullptr;
+  double* d_loss = nullptr;
 
   size_t elem() const { return precision == LBM_F64 ? sizeof(double) : sizeof(float); }
   size_t state_bytes() const { return 6 * (size_t)Ntot * elem(); }
@@ -365,7 +411,7 @@ void rebuild_tables(lbm_ctx* c) {
   }
   c->nchunks = ch;
   for (int ki = 0; ki < 4; ++ki) {
-    const long long bout = c->NT - 4 * (1 << ki);
+    const long long bout = (long long)c->NT * c->V - 4 * (1 << ki);
     long long t = 0;
     for (int b = 0; b < c->B; ++b) {
       LatDev d = c->host_lat[b];
@@ -467,7 +513,8 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   c->offset[B] = tot;
   c->Ntot = tot;
   c->K = (precision == LBM_F64) ? 1 : 4;
-  c->NT = (precision == LBM_F64) ? 512 : 1024;
+  c->NT = (precision == LBM_F64) ? 512 : 256;
+  c->V = (precision == LBM_F64) ? 1 : 2;
   rebuild_tables(c);
 
   c->d_lat = (LatDev*)dev_alloc(sizeof(LatDev) * 4 * B, c->stream);
@@ -477,11 +524,19 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   c->d_flags = (int*)dev_alloc(sizeof(int) * B, c->stream);
   c->d_part = (double*)dev_alloc(sizeof(double) * 4 * c->nchunks, c->stream);
   c->d_pflag = (int*)dev_alloc(sizeof(int) * c->nchunks, c->stream);
-  if (!c->d_lat || !c->state[0] || !c->state[1] || !c->d_sums || !c->d_flags || !c->d_part || !c->d_pflag) {
+  {
+    long long max_tiles = 0;  // narrowest tiles: 128 threads x 1 node, depth 8
+    for (int b = 0; b < B; ++b) max_tiles += (c->N[b] + (128 - 32) - 1) / (128 - 32);
+    c->d_done = (int*)dev_alloc(sizeof(int) * max_tiles, c->stream);
+  }
+  c->d_counter = (unsigned long long*)dev_alloc(sizeof(unsigned long long), c->stream);
+  c->d_status = (int*)dev_alloc(sizeof(int), c->stream);
+  if (!c->d_lat || !c->state[0] || !c->state[1] || !c->d_sums || !c->d_flags || !c->d_part || !c->d_pflag ||
+      !c->d_done || !c->d_counter || !c->d_status) {
     lbm_destroy(c);
     return LBM_ERR_OOM;
   }
-  if (upload_lat(c) != LBM_OK) {
+  if (upload_lat(c) != LBM_OK || cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ERR_CUDA;
   }
@@ -490,15 +545,61 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
 }
 
 template <typename R>
+cudaError_t enqueue_persistent(lbm_ctx* c, long long nblocks, cudaStream_t st, const lbm::ConstSet<R>& k) {
+  const int ki = depth_index(c->K);
+  cudaError_t e = cudaMemsetAsync(c->d_done, 0, sizeof(int) * c->ntiles_k[ki], st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  lbm::PersistentCtl ctl{c->d_counter, c->d_done, c->d_status, c->spin_limit, c->withhold};
+  return lbm::launch_persistent<R>((R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot, lat_for(c, c->K), c->B,
+                                   c->ntiles_k[ki], c->K, c->NT, c->V, nblocks, ctl, k, st);
+}
+
+// Persistent launch of nblocks blocks of K steps, directly or through a cached CUDA graph.
+template <typename R>
+int run_persistent(lbm_ctx* c, long long nblocks, const lbm::ConstSet<R>& k) {
+  if (c->mode == LBM_MODE_PERSISTENT) {
+    cudaError_t e = enqueue_persistent<R>(c, nblocks, c->stream, k);
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent launch");
+  } else {
+    const long long key[6] = {nblocks, c->cur, c->K, c->NT, c->V, c->spin_limit ^ (c->withhold << 40)};
+    if (!c->graph || std::memcmp(key, c->graph_key, sizeof(key)) != 0) {
+      if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+      if (!c->cap_stream) LBM_CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      LBM_CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_persistent<R>(c, nblocks, c->cap_stream, k);
+      cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "persistent capture");
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(c, e, "graph instantiate"); }
+      std::memcpy(c->graph_key, key, sizeof(key));
+    }
+    LBM_CK(c, cudaGraphLaunch(c->graph, c->stream));
+  }
+  if (nblocks & 1) c->cur = 1 - c->cur;
+  c->steps_done += nblocks * c->K;
+  return LBM_OK;
+}
+
+template <typename R>
 int run_steps(lbm_ctx* c, long long nsteps) {
-  const Consts<R> k = make_consts<R>(c->ph);
+  const lbm::ConstSet<R> k = make_constset<R>(c->ph);
   long long left = nsteps;
+  if (c->mode != LBM_MODE_LAUNCH && left >= c->K) {
+    const long long nblocks = left / c->K;
+    int rc = run_persistent<R>(c, nblocks, k);
+    if (rc != LBM_OK) return rc;
+    left -= nblocks * c->K;
+  }
   while (left > 0) {
     int K = c->K;
     while (K > left) K >>= 1;  // the remainder runs with shallower launches (same arithmetic)
     const int ki = depth_index(K);
     cudaError_t e = lbm::launch_step_tiles<R>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot,
-                                              lat_for(c, K), c->B, c->ntiles_k[ki], K, c->NT, k, c->stream, 0);
+                                              lat_for(c, K), c->B, c->ntiles_k[ki], K, c->NT, c->V, k, c->stream, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = 1 - c->cur;
     left -= K;
@@ -578,6 +679,17 @@ void lbm_destroy(lbm_ctx* c) {
   dev_free(c->d_part);
   dev_free(c->d_pflag);
   dev_free(c->d_stage);
+  dev_free(c->d_done);
+  dev_free(c->d_counter);
+  dev_free(c->d_status);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  lbm_adjoint_release(c);
+  dev_free(c->d_lat_adj);
+  dev_free(c->d_gtile);
+  dev_free(c->d_rgrad);
+  dev_free(c->d_lpart);
+  dev_free(c->d_loss);
   delete c;
 }
 
@@ -717,24 +829,23 @@ int lbm_diagnostics(lbm_ctx* c, double* sums, int32_t* flags) {
   return LBM_OK;
 }
 
-int lbm_set_config(lbm_ctx* c, int32_t k, int32_t nt) {
+int lbm_set_config(lbm_ctx* c, int32_t k, int32_t nt, int32_t v) {
   if (!c) return LBM_ERR_INVALID_ARG;
-  if (k != 0 && k != 1 && k != 2 && k != 4 && k != 8) return fail(c, LBM_ERR_INVALID_ARG, "config: k not in {1,2,4,8}");
-  if (nt != 0 && nt != 256 && nt != 512 && nt != 1024)
-    return fail(c, LBM_ERR_INVALID_ARG, "config: block_threads not in {256,512,1024}");
-  const int newK = k ? k : c->K, newNT = nt ? nt : c->NT;
-  if (newNT - 4 * newK < 32) return fail(c, LBM_ERR_INVALID_ARG, "config: tile too narrow for depth");
-  // Diagnostics scratch depends only on the lattices; tile tables on (k, NT).
+  const int newK = k ? k : c->K, newNT = nt ? nt : c->NT, newV = v ? v : c->V;
+  if (!lbm::valid_tile_config(newK, newNT, newV, c->precision == LBM_F64))
+    return fail(c, LBM_ERR_INVALID_ARG, "config: unsupported (steps_per_launch, block_threads, nodes_per_thread)");
   c->K = newK;
   c->NT = newNT;
+  c->V = newV;
   rebuild_tables(c);
   return upload_lat(c);
 }
 
-int lbm_get_config(const lbm_ctx* c, int32_t* k, int32_t* nt) {
+int lbm_get_config(const lbm_ctx* c, int32_t* k, int32_t* nt, int32_t* v) {
   if (!c) return LBM_ERR_INVALID_ARG;
   if (k) *k = c->K;
   if (nt) *nt = c->NT;
+  if (v) *v = c->V;
   return LBM_OK;
 }
 
@@ -745,43 +856,260 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
   LBM_CK(c, cudaEventCreate(&e0));
   LBM_CK(c, cudaEventCreate(&e1));
   const int Ks[4] = {1, 2, 4, 8};
-  const int NTs[3] = {256, 512, 1024};
+  const int NTs[4] = {128, 256, 512, 1024};
+  const int Vs[3] = {1, 2, 4};
   double best = 1e300;
-  int bestK = c->K, bestNT = c->NT;
+  int bestK = c->K, bestNT = c->NT, bestV = c->V;
+  const long long kTrialTiles = 16384;  // enough waves to be representative; the rest is skipped
   for (int nt : NTs)
-    for (int k : Ks) {
-      if (nt - 4 * k < 32) continue;
-      c->K = k;
-      c->NT = nt;
-      rebuild_tables(c);
-      int rc = upload_lat(c);
-      if (rc) return rc;
-      float ms = 0.f;
-      for (int t = 0; t <= trials; ++t) {  // first launch is a warm-up
-        if (t == 1) LBM_CK(c, cudaEventRecord(e0, c->stream));
-        cudaError_t e;
-        if (c->precision == LBM_F64)
-          e = lbm::launch_step_tiles<double>((const double*)c->state[c->cur], (double*)c->state[1 - c->cur], c->Ntot,
-                                             lat_for(c, k), c->B, c->ntiles, k, nt, make_consts<double>(c->ph),
-                                             c->stream, 0);
-        else
-          e = lbm::launch_step_tiles<float>((const float*)c->state[c->cur], (float*)c->state[1 - c->cur], c->Ntot,
-                                            lat_for(c, k), c->B, c->ntiles, k, nt, make_consts<float>(c->ph),
-                                            c->stream, 0);
-        if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
+    for (int v : Vs)
+      for (int k : Ks) {
+        if (!lbm::valid_tile_config(k, nt, v, c->precision == LBM_F64)) continue;
+        c->K = k;
+        c->NT = nt;
+        c->V = v;
+        rebuild_tables(c);
+        int rc = upload_lat(c);
+        if (rc) return rc;
+        const long long nt_run = std::min(c->ntiles, kTrialTiles);
+        const double nodes = (double)nt_run * (nt * v - 4 * k);
+        float ms = 0.f;
+        for (int t = 0; t <= trials; ++t) {  // the first launch is a warm-up
+          if (t == 1) LBM_CK(c, cudaEventRecord(e0, c->stream));
+          cudaError_t e;
+          if (c->precision == LBM_F64)
+            e = lbm::launch_step_tiles<double>((const double*)c->state[c->cur], (double*)c->state[1 - c->cur],
+                                               c->Ntot, lat_for(c, k), c->B, nt_run, k, nt, v,
+                                               make_constset<double>(c->ph), c->stream, 0);
+          else
+            e = lbm::launch_step_tiles<float>((const float*)c->state[c->cur], (float*)c->state[1 - c->cur],
+                                              c->Ntot, lat_for(c, k), c->B, nt_run, k, nt, v,
+                                              make_constset<float>(c->ph), c->stream, 0);
+          if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
+        }
+        LBM_CK(c, cudaEventRecord(e1, c->stream));
+        LBM_CK(c, cudaEventSynchronize(e1));
+        LBM_CK(c, cudaEventElapsedTime(&ms, e0, e1));
+        const double per_node_step = ms / (trials * k * nodes);
+        if (per_node_step < best) { best = per_node_step; bestK = k; bestNT = nt; bestV = v; }
       }
-      LBM_CK(c, cudaEventRecord(e1, c->stream));
-      LBM_CK(c, cudaEventSynchronize(e1));
-      LBM_CK(c, cudaEventElapsedTime(&ms, e0, e1));
-      const double per_step = ms / (double)(trials * k);
-      if (per_step < best) { best = per_step; bestK = k; bestNT = nt; }
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->K = bestK;
   c->NT = bestNT;
+  c->V = bestV;
   rebuild_tables(c);
   return upload_lat(c);
+}
+
+int lbm_set_mode(lbm_ctx* c, int32_t mode) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (mode != LBM_MODE_LAUNCH && mode != LBM_MODE_PERSISTENT && mode != LBM_MODE_PERSISTENT_GRAPH)
+    return fail(c, LBM_ERR_INVALID_ARG, "set_mode: unknown mode");
+  c->mode = mode;
+  return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  int st = 0;
+  LBM_CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  if (st != 0) {
+    LBM_CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the persistent kernel expired; the state is not valid");
+  }
+  return LBM_OK;
+}
+
+int lbm_debug_persistent(lbm_ctx* c, int64_t spin_limit, int64_t withhold_tile) {
+  if (!c || spin_limit < 1) return LBM_ERR_INVALID_ARG;
+  c->spin_limit = spin_limit;
+  c->withhold = withhold_tile < 0 ? -1 : withhold_tile;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint with sqrt(T) checkpointing.
+
+namespace {
+
+int adjoint_setup(lbm_ctx* c) {
+  if (c->d_lat_adj) return LBM_OK;
+  std::vector<LatDev> tab(c->host_lat);
+  const long long bout = lbm::kAdjointThreads - 4;
+  long long t = 0;
+  for (int b = 0; b < c->B; ++b) {
+    tab[b].tile0 = t;
+    t += (c->N[b] + bout - 1) / bout;
+  }
+  c->adj_ntiles = t;
+  c->d_lat_adj = (LatDev*)dev_alloc(sizeof(LatDev) * c->B, c->stream);
+  c->d_gtile = (double*)dev_alloc(sizeof(double) * 2 * t, c->stream);
+  c->d_rgrad = (double*)dev_alloc(sizeof(double) * 2 * c->B, c->stream);
+  c->d_lpart = (double*)dev_alloc(sizeof(double) * ((c->Ntot + 255) / 256), c->stream);
+  c->d_loss = (double*)dev_alloc(sizeof(double), c->stream);
+  if (!c->d_lat_adj || !c->d_gtile || !c->d_rgrad || !c->d_lpart || !c->d_loss)
+    return fail(c, LBM_ERR_OOM, "adjoint: allocation failed");
+  LBM_CK(c, cudaMemcpyAsync(c->d_lat_adj, tab.data(), sizeof(LatDev) * c->B, cudaMemcpyHostToDevice, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+template <typename R>
+int adjoint_forward_impl(lbm_ctx* c, long long T) {
+  int rc = adjoint_setup(c);
+  if (rc) return rc;
+  lbm_adjoint_release(c);
+  long long seg = (long long)std::llround(std::sqrt((double)T));
+  if (seg < 1) seg = 1;
+  const long long nseg = (T + seg - 1) / seg > 0 ? (T + seg - 1) / seg : 1;
+  const size_t sb = c->state_bytes();
+  for (long long j = 0; j < nseg; ++j) {
+    void* p = dev_alloc(sb, c->stream);
+    if (!p) { lbm_adjoint_release(c); return fail(c, LBM_ERR_OOM, "adjoint: checkpoint allocation failed"); }
+    c->ckpt.push_back(p);
+  }
+  for (long long j = 0; j + 1 < seg; ++j) {
+    void* p = dev_alloc(sb, c->stream);
+    if (!p) { lbm_adjoint_release(c); return fail(c, LBM_ERR_OOM, "adjoint: stash allocation failed"); }
+    c->stash.push_back(p);
+  }
+  for (int k = 0; k < 2; ++k) {
+    c->adj_a[k] = dev_alloc(sb, c->stream);
+    if (!c->adj_a[k]) { lbm_adjoint_release(c); return fail(c, LBM_ERR_OOM, "adjoint: buffer allocation failed"); }
+  }
+  const int save_mode = c->mode;
+  c->mode = LBM_MODE_LAUNCH;
+  for (long long j = 0; j < nseg; ++j) {
+    LBM_CK(c, cudaMemcpyAsync(c->ckpt[j], c->state[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
+    const long long len = std::min(seg, T - j * seg);
+    rc = run_steps<R>(c, len);
+    if (rc) { c->mode = save_mode; return rc; }
+  }
+  c->mode = save_mode;
+  c->adj_T = T;
+  c->adj_seg = seg;
+  c->adj_nseg = nseg;
+  return LBM_OK;
+}
+
+// Reverse sweep from the seed already in adj_a[0]; leaves dL/df(0) in adj_a[res].
+template <typename R>
+int adjoint_reverse(lbm_ctx* c, int* res) {
+  const lbm::ConstSet<R> k = make_constset<R>(c->ph);
+  LBM_CK(c, cudaMemsetAsync(c->d_gtile, 0, sizeof(double) * 2 * c->adj_ntiles, c->stream));
+  int a = 0;
+  for (long long j = c->adj_nseg - 1; j >= 0; --j) {
+    const long long len = std::min(c->adj_seg, c->adj_T - j * c->adj_seg);
+    // States t0 .. t0 + len - 1 of this segment: the checkpoint, then recomputed one step at a time.
+    std::vector<const R*> st(len);
+    st[0] = (const R*)c->ckpt[j];
+    for (long long i = 1; i < len; ++i) {
+      cudaError_t e = lbm::launch_step_tiles<R>(st[i - 1], (R*)c->stash[i - 1], c->Ntot, lat_for(c, 1), c->B,
+                                                c->ntiles_k[0], 1, c->NT, c->V, k, c->stream, 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint recompute");
+      st[i] = (const R*)c->stash[i - 1];
+    }
+    for (long long i = len - 1; i >= 0; --i) {
+      cudaError_t e = lbm::launch_adjoint_step<R>(st[i], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot,
+                                                  c->d_lat_adj, c->B, c->adj_ntiles, k.s, c->d_gtile, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
+      a = 1 - a;
+    }
+  }
+  *res = a;
+  return LBM_OK;
+}
+
+template <typename R>
+int adjoint_backward_impl(lbm_ctx* c, const double* target, const double* rho_b, double* loss, double* drho0,
+                          double* du0, double* drates, double* dfd0) {
+  if (c->adj_T < 0) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: no forward run recorded");
+  const long long n = c->Ntot;
+  // Inputs: stage a host target / seed on the device.
+  const double* in = target ? target : rho_b;
+  const bool host_in = !is_device_ptr(in);
+  int rc = ensure_stage(c, sizeof(double) * n * 9);
+  if (rc) return rc;
+  const double* d_in = in;
+  if (host_in) {
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage, in, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    d_in = c->d_stage;
+  }
+  cudaError_t e = lbm::launch_misfit_seed<R>((const R*)c->state[c->cur], target ? d_in : nullptr,
+                                             target ? nullptr : d_in, n, c->ph.rho0, (R*)c->adj_a[0], c->d_lpart,
+                                             c->d_loss, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint seed");
+  int a = 0;
+  rc = adjoint_reverse<R>(c, &a);
+  if (rc) return rc;
+  double* d_drho = c->d_stage + n;
+  double* d_du = c->d_stage + 2 * n;
+  e = lbm::launch_adjoint_init<R>((const R*)c->ckpt[0], (const R*)c->adj_a[a], n, c->d_lat, c->B,
+                                  make_consts<double>(c->ph), d_drho, d_du, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint init");
+  e = lbm::launch_reduce_rate_grads(c->d_gtile, c->d_lat_adj, c->B, c->adj_ntiles, c->d_rgrad, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint rate reduction");
+  if (dfd0) {
+    // dL/df(0) as float64 (the population shift is a constant and does not change the gradient).
+    double* dst = is_device_ptr(dfd0) ? dfd0 : c->d_stage + 3 * n;
+    e = lbm::launch_to_f64<R>((const R*)c->adj_a[a], dst, 6 * n, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint output");
+    if (dst != dfd0) LBM_CK(c, cudaMemcpyAsync(dfd0, dst, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (drho0) LBM_CK(c, cudaMemcpyAsync(drho0, d_drho, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+  if (du0) LBM_CK(c, cudaMemcpyAsync(du0, d_du, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+  if (drates) LBM_CK(c, cudaMemcpyAsync(drates, c->d_rgrad, sizeof(double) * 2 * c->B, cudaMemcpyDefault, c->stream));
+  if (loss && target) LBM_CK(c, cudaMemcpyAsync(loss, c->d_loss, sizeof(double), cudaMemcpyDefault, c->stream));
+  LBM_CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_adjoint_forward(lbm_ctx* c, int64_t T) {
+  if (!c || T < 1) return LBM_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: no state set");
+  return c->precision == LBM_F64 ? adjoint_forward_impl<double>(c, T) : adjoint_forward_impl<float>(c, T);
+}
+
+int lbm_adjoint_backward(lbm_ctx* c, const double* dL_drho_T, double* dL_drho0, double* dL_du0, double* dL_drates,
+                         double* dL_dfd0) {
+  if (!c || !dL_drho_T) return LBM_ERR_INVALID_ARG;
+  return c->precision == LBM_F64
+             ? adjoint_backward_impl<double>(c, nullptr, dL_drho_T, nullptr, dL_drho0, dL_du0, dL_drates, dL_dfd0)
+             : adjoint_backward_impl<float>(c, nullptr, dL_drho_T, nullptr, dL_drho0, dL_du0, dL_drates, dL_dfd0);
+}
+
+int lbm_adjoint(lbm_ctx* c, int64_t T, const double* rho_target, double* loss, double* dL_drho0, double* dL_du0,
+                double* dL_drates) {
+  if (!c || !rho_target || T < 1) return LBM_ERR_INVALID_ARG;
+  int rc = lbm_adjoint_forward(c, T);
+  if (rc) return rc;
+  return c->precision == LBM_F64
+             ? adjoint_backward_impl<double>(c, rho_target, nullptr, loss, dL_drho0, dL_du0, dL_drates, nullptr)
+             : adjoint_backward_impl<float>(c, rho_target, nullptr, loss, dL_drho0, dL_du0, dL_drates, nullptr);
+}
+
+int lbm_adjoint_release(lbm_ctx* c) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  if (!c->ckpt.empty() || !c->stash.empty() || c->adj_a[0] || c->adj_a[1]) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+  }
+  for (void* p : c->ckpt) dev_free(p);
+  for (void* p : c->stash) dev_free(p);
+  c->ckpt.clear();
+  c->stash.clear();
+  for (int k = 0; k < 2; ++k) { dev_free(c->adj_a[k]); c->adj_a[k] = nullptr; }
+  c->adj_T = -1;
+  return LBM_OK;
 }
 
 // Checkpoint format: magic, version, precision, B, the physical constants, per-lattice

@@ -21,99 +21,205 @@ struct LatDev {
   int bc, pad;
 };
 
-// Constants shared by all lattices, converted to the arithmetic type R on the host.
-template <typename R>
+// Constants shared by all lattices, converted on the host to the lane type X the node arithmetic
+// runs in: double, float, or float2 (two nodes per lane for Blackwell's paired FP32 instructions;
+// every field then holds the same value twice, so it can be an operand of a paired instruction).
+template <typename X>
 struct Consts {
-  R rho0, lam, two_lam2;          // rho0, lambda, 2 lambda^2
-  R inv_af, inv_af_l, inv_af_l2;  // 1/rho0, 1/(rho0 lambda), 1/(rho0 lambda^2)
-  R af_l, af_l2;                  // rho0 lambda, rho0 lambda^2
-  R ag, ag_l, ag_l2;              // rho0 c_p, rho0 c_p lambda, rho0 c_p lambda^2
-  R inv_ag, inv_ag_l, inv_ag_l2;
-  R gamma, inv_cp, p0, inv_r;     // gamma, 1/c_p, p0, 1/r with r = c_p (1 - 1/gamma)
-  R e_r;                          // 3 p0 - 2 lambda^2 rho0
-  R cp_log;                       // (1 - 1/gamma) c_p
-  R cp_over_Pr;                   // c_p / Pr
+  X rho0, lam, two_lam2;          // rho0, lambda, 2 lambda^2
+  X inv_af, inv_af_l, inv_af_l2;  // 1/rho0, 1/(rho0 lambda), 1/(rho0 lambda^2)
+  X af_l, af_l2;                  // rho0 lambda, rho0 lambda^2
+  X ag, ag_l, ag_l2;              // rho0 c_p, rho0 c_p lambda, rho0 c_p lambda^2
+  X inv_ag, inv_ag_l, inv_ag_l2;
+  X gamma, inv_cp, p0, inv_r;     // gamma, 1/c_p, p0, 1/r with r = c_p (1 - 1/gamma)
+  X e_r;                          // 3 p0 - 2 lambda^2 rho0
+  X cp_log;                       // (1 - 1/gamma) c_p
+  X cp_over_Pr;                   // c_p / Pr
+  X m_two_lam2;                   // -2 lambda^2
+  X one, m_one, two, m_two, three, half, m_half, third, sixth;  // numeric constants
   int source_on;
 };
 
-__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+// Lane arithmetic: add, sub, mul, fused multiply-add, reciprocal.
+__device__ __forceinline__ float ad(float a, float b) { return a + b; }
+__device__ __forceinline__ double ad(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 ad(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float sb(float a, float b) { return a - b; }
+__device__ __forceinline__ double sb(double a, double b) { return a - b; }
+__device__ __forceinline__ float2 sb(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float ml(float a, float b) { return a * b; }
+__device__ __forceinline__ double ml(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 ml(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 fm(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// Reciprocals: FP32 uses the hardware approximation (at most 2 ulp in the normal range), FP64 the
+// correctly rounded reciprocal.
+__device__ __forceinline__ float m_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double m_rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); }
+
+// log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes the common
+// range is evaluated with textbook series in paired arithmetic, the rest with CUDA's functions:
+//  - log1p(x) = 2 atanh(z), z = x / (2 + x) = 2 z (1 + w/3 + w^2/5 + w^3/7 + w^4/9 + w^5/11), w = z^2,
+//    for |x| <= 0.3 (|z| <= 0.177: the first omitted term is below 1e-9 relative);
+//  - expm1(x) = x + x^2 (1/2! + x/3! + ... + x^7/9!) for |x| <= 0.35 (first omitted term below
+//    1e-9 relative).
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
-__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
-
-// Moments and thermodynamic state of one node from its shifted populations
-// ft = f - w (order f0, f+, f-, g0, g+, g-). Everything returned is a deviation from the rest
-// state where marked "t" (tilde).
-template <typename R>
-struct Node {
-  R rt, J, et;       // rho - rho0, J, e - e_r
-  R zt, psi, epst;   // zeta - zeta_r, psi, eps - eps_r
-  R rho, inv_rho, u, ds, lnr, pt, T;  // rho, 1/rho, u, s - s0, log(rho/rho0), p - p0, T
-};
-
-template <typename R>
-__device__ __forceinline__ void node_state(const R f[6], const Consts<R>& c, R s0, Node<R>& m) {
-  // (ii) m = M f_d, eq. (M-d1q3q3), applied to the deviations from the rest populations.
-  m.rt = c.rho0 * (f[0] + f[1] + f[2]);
-  m.J = c.af_l * (f[1] - f[2]);
-  m.et = c.af_l2 * (f[1] + f[2] - R(2) * f[0]);
-  m.zt = c.ag * (f[3] + f[4] + f[5]);
-  m.psi = c.ag_l * (f[4] - f[5]);
-  m.epst = c.ag_l2 * (f[4] + f[5] - R(2) * f[3]);
-  // Thermodynamics, eq. (gaz-parfait): p = p0 (rho/rho0)^gamma exp(gamma (s - s0)/c_p), p = rho r T.
-  m.rho = c.rho0 + m.rt;
-  m.inv_rho = R(1) / m.rho;
-  m.u = m.J * m.inv_rho;
-  m.ds = (m.zt - m.rt * s0) * m.inv_rho;  // zeta - rho s0 = zeta_t - rho_t s0
-  m.lnr = m_log1p(m.rt * c.inv_af);
-  m.pt = c.p0 * m_expm1(c.gamma * (m.lnr + m.ds * c.inv_cp));
-  m.T = (c.p0 + m.pt) * m.inv_rho * c.inv_r;
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ float2 m_log1p(float2 x) {
+  if (fabsf(x.x) > 0.3f || fabsf(x.y) > 0.3f) return make_float2(log1pf(x.x), log1pf(x.y));
+  const float2 d = __fadd2_rn(x, make_float2(2.0f, 2.0f));
+  float2 y = m_rcp(d);
+  y = __ffma2_rn(y, __ffma2_rn(make_float2(-d.x, -d.y), y, make_float2(1.0f, 1.0f)), y);  // Newton step
+  const float2 z = __fmul2_rn(x, y);
+  const float2 w = __fmul2_rn(z, z);
+  float2 p = make_float2(1.0f / 11.0f, 1.0f / 11.0f);
+  p = __ffma2_rn(p, w, make_float2(1.0f / 9.0f, 1.0f / 9.0f));
+  p = __ffma2_rn(p, w, make_float2(1.0f / 7.0f, 1.0f / 7.0f));
+  p = __ffma2_rn(p, w, make_float2(1.0f / 5.0f, 1.0f / 5.0f));
+  p = __ffma2_rn(p, w, make_float2(1.0f / 3.0f, 1.0f / 3.0f));
+  const float2 z2 = __fadd2_rn(z, z);
+  return __ffma2_rn(__fmul2_rn(z2, w), p, z2);
+}
+__device__ __forceinline__ float2 m_expm1(float2 x) {
+  if (fabsf(x.x) > 0.35f || fabsf(x.y) > 0.35f) return make_float2(expm1f(x.x), expm1f(x.y));
+  float2 p = make_float2(1.0f / 362880.0f, 1.0f / 362880.0f);
+  p = __ffma2_rn(p, x, make_float2(1.0f / 40320.0f, 1.0f / 40320.0f));
+  p = __ffma2_rn(p, x, make_float2(1.0f / 5040.0f, 1.0f / 5040.0f));
+  p = __ffma2_rn(p, x, make_float2(1.0f / 720.0f, 1.0f / 720.0f));
+  p = __ffma2_rn(p, x, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+  p = __ffma2_rn(p, x, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+  p = __ffma2_rn(p, x, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+  p = __ffma2_rn(p, x, make_float2(0.5f, 0.5f));
+  return __ffma2_rn(__fmul2_rn(x, x), p, x);
 }
 
-// Steps (iv)-(vii) for one node: equilibria, relaxation, entropy source; returns the shifted
+// Moments and thermodynamic state of one node (or node pair) from its shifted populations
+// f - w (order f0, f+, f-, g0, g+, g-). Fields marked "t" (tilde) are deviations from the rest state.
+template <typename X>
+struct Node {
+  X rt, J, et;       // rho - rho0, J, e - e_r
+  X zt, psi, epst;   // zeta - zeta_r, psi, eps - eps_r
+  X rho, inv_rho, u, ds, lnr, pt, T;  // rho, 1/rho, u, s - s0, log(rho/rho0), p - p0, T
+};
+
+template <typename X>
+__device__ __forceinline__ void node_state(const X f[6], const Consts<X>& c, X s0, Node<X>& m) {
+  // (ii) m = M f_d, eq. (M-d1q3q3), applied to the deviations from the rest populations.
+  const X tf = ad(f[1], f[2]), tg = ad(f[4], f[5]);
+  m.rt = ml(c.rho0, ad(tf, f[0]));
+  m.J = ml(c.af_l, sb(f[1], f[2]));
+  m.et = ml(c.af_l2, fm(f[0], c.m_two, tf));
+  m.zt = ml(c.ag, ad(tg, f[3]));
+  m.psi = ml(c.ag_l, sb(f[4], f[5]));
+  m.epst = ml(c.ag_l2, fm(f[3], c.m_two, tg));
+  // Thermodynamics, eq. (gaz-parfait): p = p0 (rho/rho0)^gamma exp(gamma (s - s0)/c_p), p = rho r T.
+  m.rho = ad(c.rho0, m.rt);
+  m.inv_rho = m_rcp(m.rho);
+  m.u = ml(m.J, m.inv_rho);
+  m.ds = ml(fm(m.rt, sb(X{}, s0), m.zt), m.inv_rho);  // zeta - rho s0 = zeta_t - rho_t s0
+  m.lnr = m_log1p(ml(m.rt, c.inv_af));
+  m.pt = ml(c.p0, m_expm1(ml(c.gamma, fm(m.ds, c.inv_cp, m.lnr))));
+  m.T = ml(ml(ad(c.p0, m.pt), m.inv_rho), c.inv_r);
+}
+
+// Steps (iv)-(vii) for one node (pair): equilibria, relaxation, entropy source; returns the shifted
 // post-collision populations fs = M^{-1} m* - w.
-template <typename R>
-__device__ __forceinline__ void node_collide(const Node<R>& m, R ul, R ur, R Tl, R Tr, R s_e, R s_psi,
-                                             R s_eps, R q_src, R s0, const Consts<R>& c, R fs[6]) {
+template <typename X>
+__device__ __forceinline__ void node_collide(const Node<X>& m, X ul, X ur, X Tl, X Tr, X s_e, X s_psi, X s_eps,
+                                             X q_src, X s0, const Consts<X>& c, X fs[6]) {
   // (iv) equilibria: e_eq (eq. energie-equilibre), psi_eq = zeta u (eq. psi-equilibre), and the
   // polytropic form of eq. (eq-energie-entropie-d1q3q3), all as deviations from the rest state.
-  const R s = s0 + m.ds;
-  const R zeta = m.rho * s;
-  const R e_eq_t = R(3) * (m.J * m.u + m.pt) - c.two_lam2 * m.rt;
-  const R psi_eq = zeta * m.u;
-  const R eps_eq_t = c.two_lam2 * m.rho * (m.ds + c.cp_log * m.lnr) + e_eq_t * s + c.e_r * m.ds;
+  const X s = ad(s0, m.ds);
+  const X zeta = ml(m.rho, s);
+  const X e_eq_t = fm(m.rt, c.m_two_lam2, ml(c.three, fm(m.J, m.u, m.pt)));
+  const X psi_eq = ml(zeta, m.u);
+  const X eps_eq_t = fm(c.e_r, m.ds, fm(e_eq_t, s, ml(ml(c.two_lam2, m.rho), fm(c.cp_log, m.lnr, m.ds))));
   // (v) relaxation, eq. (relaxation-d1q3q3).
-  const R es = m.et + s_e * (e_eq_t - m.et);
-  const R psis = m.psi + s_psi * (psi_eq - m.psi);
-  const R epss = m.epst + s_eps * (eps_eq_t - m.epst);
+  const X es = fm(s_e, sb(e_eq_t, m.et), m.et);
+  const X psis = fm(s_psi, sb(psi_eq, m.psi), m.psi);
+  const X epss = fm(s_eps, sb(eps_eq_t, m.epst), m.epst);
   // (vii) entropy production of eq. (NS-rho-J-zeta) with centred differences, added to zeta.
-  R zs = m.zt;
+  X zs = m.zt;
   if (c.source_on) {
-    const R du = ur - ul, dT = Tr - Tl;
-    const R inv_T = R(1) / m.T;
-    zs += q_src * m.rho * inv_T * (du * du + c.cp_over_Pr * dT * dT * inv_T);
+    const X du = sb(ur, ul), dT = sb(Tr, Tl);
+    const X inv_T = m_rcp(m.T);
+    const X A = fm(ml(c.cp_over_Pr, ml(dT, dT)), inv_T, ml(du, du));
+    zs = fm(ml(ml(q_src, m.rho), inv_T), A, m.zt);
   }
   // (vi) f_d* = M^{-1} m*, block by block: x0 = (r - q)/3, x+- = (2r + q)/6 +- j/2.
   {
-    const R r = m.rt * c.inv_af, j = m.J * c.inv_af_l, q = es * c.inv_af_l2;
-    const R h = (R(2) * r + q) * R(1.0 / 6.0);
-    fs[0] = (r - q) * R(1.0 / 3.0);
-    fs[1] = h + R(0.5) * j;
-    fs[2] = h - R(0.5) * j;
+    const X r = ml(m.rt, c.inv_af), j = ml(m.J, c.inv_af_l), q = ml(es, c.inv_af_l2);
+    const X h = ml(fm(r, c.two, q), c.sixth);
+    fs[0] = ml(sb(r, q), c.third);
+    fs[1] = fm(j, c.half, h);
+    fs[2] = fm(j, c.m_half, h);
   }
   {
-    const R r = zs * c.inv_ag, j = psis * c.inv_ag_l, q = epss * c.inv_ag_l2;
-    const R h = (R(2) * r + q) * R(1.0 / 6.0);
-    fs[3] = (r - q) * R(1.0 / 3.0);
-    fs[4] = h + R(0.5) * j;
-    fs[5] = h - R(0.5) * j;
+    const X r = ml(zs, c.inv_ag), j = ml(psis, c.inv_ag_l), q = ml(epss, c.inv_ag_l2);
+    const X h = ml(fm(r, c.two, q), c.sixth);
+    fs[3] = ml(sb(r, q), c.third);
+    fs[4] = fm(j, c.half, h);
+    fs[5] = fm(j, c.m_half, h);
   }
 }
 
-// Host-side launchers (lbm_step.cu).
+// The constants in the scalar type R and, for FP32, also broadcast to paired lanes.
+template <typename R>
+struct ConstSet {
+  Consts<R> s;
+  Consts<float2> p;
+  template <typename X>
+  const Consts<X>& get() const;
+};
+template <>
+template <>
+inline const Consts<double>& ConstSet<double>::get<double>() const { return s; }
+template <>
+template <>
+inline const Consts<float>& ConstSet<float>::get<float>() const { return s; }
+template <>
+template <>
+inline const Consts<float2>& ConstSet<float>::get<float2>() const { return p; }
+
+// Host-side launchers (lbm_step.cu). A tile has NT threads of V nodes; K steps per launch.
+// Only the first ntiles tiles are processed (the autotuner times partial launches).
 template <typename R>
 cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, int B,
-                              long long ntiles, int K, int NT, const Consts<R>& c, cudaStream_t st,
-                              int grid_cap);
+                              long long ntiles, int K, int NT, int V, const ConstSet<R>& c, cudaStream_t st,
+                              long long grid_cap);
+bool valid_tile_config(int K, int NT, int V, bool fp64);
+
+// Control block of the persistent launch (device pointers).
+struct PersistentCtl {
+  unsigned long long* counter;  // next work unit
+  int* done;                    // per tile: number of finished time blocks
+  int* status;                  // 0, or 1 once a bounded wait has expired
+  long long spin_limit;         // polls (about 100 ns apart) before a wait gives up
+  long long withhold;           // test hook: tile whose first block is never published (-1: none)
+};
+template <typename R>
+cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, int B, long long ntiles, int K,
+                              int NT, int V, long long nblocks, const PersistentCtl& ctl, const ConstSet<R>& c,
+                              cudaStream_t st);
+
+// Adjoint (lbm_adjoint.cu): one step per launch, tiles of kAdjointThreads nodes (halo 2 per side).
+constexpr int kAdjointThreads = 256;
+template <typename R>
+cudaError_t launch_adjoint_step(const R* fin, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
+                                long long ntiles, const Consts<R>& c, double* grad_tile, cudaStream_t st);
+cudaError_t launch_reduce_rate_grads(const double* grad_tile, const LatDev* lat, int B, long long ntiles, double* out,
+                                     cudaStream_t st);
+template <typename R>
+cudaError_t launch_adjoint_init(const R* f0, const R* a0, long long plane, const LatDev* lat, int B,
+                                const Consts<double>& c, double* drho, double* du, cudaStream_t st);
+template <typename R>
+cudaError_t launch_to_f64(const R* in, double* out, long long n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_misfit_seed(const R* fT, const double* target, const double* rho_b, long long plane, double rho0,
+                               R* aT, double* part, double* loss, cudaStream_t st);
 
 }  // namespace lbm

@@ -1,122 +1,410 @@
 // Fused collide-stream kernel of the D1Q3Q3 scheme (section 8, steps (i)-(viii)) with temporal
-// blocking: one CTA loads a tile of NT consecutive nodes of one lattice (structure-of-arrays, six
-// coalesced plane loads), advances it K time steps in registers and shared memory, and stores the
-// NT - 4K interior nodes whose dependency cone (radius 2 per step: the source needs u and T of
-// the neighbours, streaming moves one node) stayed inside the tile.
+// blocking.
 //
-// Per step and node: the moments, u and T are computed in registers; u and T go to shared memory;
-// after a barrier each node reads its neighbours' u and T, collides, and writes its moving
-// populations (f+, f-, g+, g-) into the neighbour's slot of four exchange arrays; after a second
-// barrier each node picks up its streamed populations. f0 and g0 never leave registers.
+// A CTA of NT threads owns a tile of NT*V consecutive nodes of one lattice; thread t holds nodes
+// t*V .. t*V + V - 1 in registers (structure-of-arrays loads of the six population planes). The
+// tile advances K time steps without touching HBM and stores its NT*V - 4K interior nodes: the
+// dependency radius is 2 per step (the source needs u and T of the neighbours; streaming moves one
+// node), so 2K halo nodes on each side are recomputed and discarded.
+//
+// Per step: every node computes its moments, u and T; neighbours' u and T come from the same
+// thread's registers, from the adjacent lane (warp shuffle) or, at warp edges, from two words of
+// shared memory per warp. After the collision every node pulls its incoming moving populations
+// (f+, g+ from the left, f-, g- from the right) the same way. f0 and g0 never move. A wall node
+// (bounce-back) takes its own reflected population instead. Two CTA barriers per step.
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
-                                                        long long plane, const LatDev* __restrict__ lat,
-                                                        int B, long long ntiles, int K, Consts<R> c) {
-  __shared__ R su[NT];
-  __shared__ R sT[NT];
-  __shared__ R xfp[NT + 1];  // xfp[n] receives f+* of node n - 1
-  __shared__ R xfm[NT + 1];  // xfm[n + 1] receives f-* of node n + 1
-  __shared__ R xgp[NT + 1];
-  __shared__ R xgm[NT + 1];
-  const int n = threadIdx.x;
-  if (n == 0) {
-    // Edge slots no node writes: the two outermost nodes of a tile read them and are discarded.
-    xfp[0] = R(0); xgp[0] = R(0); xfm[NT] = R(0); xgm[NT] = R(0);
-  }
+template <typename R, bool CG>
+__device__ __forceinline__ R ld_state(const R* p) {
+  if constexpr (CG) return __ldcg(p);  // L2 only: the persistent kernel reads data other CTAs wrote
+  else return *p;
+}
+
+// Advances one tile K steps: reads `in`, writes the interior of the tile to `out`.
+template <typename R, int NT, int V, bool CG>
+__device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, const LatDev& d, long long start,
+                                          int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4]) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int halo = 2 * K;
-  const int bout = NT - 2 * halo;
+  const int bout = NT * V - 2 * halo;
+  const long long off = d.offset, N = d.n;
+  const int bc = d.bc;
+  const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0 = R(d.s0);
+  const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int L = 0;
-    if (B > 1) {  // last lattice whose first tile is <= tile
-      int lo = 0, hi = B - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-      }
-      L = lo;
-    }
-    const long long off = lat[L].offset, N = lat[L].n;
-    const int bc = lat[L].bc;
-    const R s_e = R(lat[L].s_e), s_psi = R(lat[L].s_psi), s_eps = R(lat[L].s_eps);
-    const R q_src = R(lat[L].q_src), s0 = R(lat[L].s0);
-
-    const long long start = (tile - lat[L].tile0) * bout;
-    const long long pos = start - halo + n;  // lattice-relative position of this thread's node
+  R f[V][6];
+  bool lw[V], rw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const long long pos = pos0 + v;
     long long lp = pos;
     if (bc == 0) {
       if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
     } else {
       lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
-    const bool active = (bc == 0) || (pos >= 0 && pos < N);
-    const bool lwall = (bc != 0) && pos == 0;
-    const bool rwall = (bc != 0) && pos == N - 1;
-
-    R f[6];
-    const long long g = off + lp;
+    lw[v] = (bc != 0) && pos == 0;
+    rw[v] = (bc != 0) && pos == N - 1;
+    const R* src = in + off + lp;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) f[i] = in[i * plane + g];
+    for (int i = 0; i < 6; ++i) f[v][i] = ld_state<R, CG>(src + i * plane);
+  }
 
-    for (int k = 0; k < K; ++k) {
-      Node<R> m;
-      node_state(f, c, s0, m);
-      su[n] = m.u;
-      sT[n] = m.T;
-      __syncthreads();
-      R ul = n > 0 ? su[n - 1] : m.u, Tl = n > 0 ? sT[n - 1] : m.T;
-      R ur = n < NT - 1 ? su[n + 1] : m.u, Tr = n < NT - 1 ? sT[n + 1] : m.T;
-      if (lwall) { ul = -m.u; Tl = m.T; }
-      if (rwall) { ur = -m.u; Tr = m.T; }
-      R fs[6];
-      node_collide(m, ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0, c, fs);
-      f[0] = fs[0];
-      f[3] = fs[3];
-      if (active) {
-        // (viii) streaming; at a wall the outgoing population comes back reversed.
-        if (rwall) { xfm[n + 1] = fs[1]; xgm[n + 1] = fs[4]; }
-        else { xfp[n + 1] = fs[1]; xgp[n + 1] = fs[4]; }
-        if (lwall) { xfp[n] = fs[2]; xgp[n] = fs[5]; }
-        else { xfm[n] = fs[2]; xgm[n] = fs[5]; }
-      }
-      __syncthreads();
-      f[1] = xfp[n];
-      f[4] = xgp[n];
-      f[2] = xfm[n + 1];
-      f[5] = xgm[n + 1];
+  for (int k = 0; k < K; ++k) {
+    Node<R> m[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) node_state(f[v], c, s0, m[v]);
+    // u, T of the neighbours of the first and last node of this thread.
+    R uL = __shfl_up_sync(0xffffffffu, m[V - 1].u, 1), TL = __shfl_up_sync(0xffffffffu, m[V - 1].T, 1);
+    R uR = __shfl_down_sync(0xffffffffu, m[0].u, 1), TR = __shfl_down_sync(0xffffffffu, m[0].T, 1);
+    if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].T; }
+    if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].T; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
+
+    R fs[V][6];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      R ul = v > 0 ? m[v - 1].u : uL, Tl = v > 0 ? m[v - 1].T : TL;
+      R ur = v < V - 1 ? m[v + 1].u : uR, Tr = v < V - 1 ? m[v + 1].T : TR;
+      if (lw[v]) { ul = -m[v].u; Tl = m[v].T; }
+      if (rw[v]) { ur = -m[v].u; Tr = m[v].T; }
+      node_collide(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0, c, fs[v]);
     }
-
-    if (n >= halo && n < halo + bout && pos < N) {
-      const long long o = off + pos;
+    // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
+    R fpL = __shfl_up_sync(0xffffffffu, fs[V - 1][1], 1), gpL = __shfl_up_sync(0xffffffffu, fs[V - 1][4], 1);
+    R fmR = __shfl_down_sync(0xffffffffu, fs[0][2], 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5], 1);
+    if (lane == 31) { e_f[warp][0] = fs[V - 1][1]; e_f[warp][1] = fs[V - 1][4]; }
+    if (lane == 0) { e_f[warp][2] = fs[0][2]; e_f[warp][3] = fs[0][5]; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
 #pragma unroll
-      for (int i = 0; i < 6; ++i) out[i * plane + o] = f[i];
+    for (int v = 0; v < V; ++v) {
+      f[v][0] = fs[v][0];
+      f[v][3] = fs[v][3];
+      f[v][1] = lw[v] ? fs[v][2] : (v > 0 ? fs[v - 1][1] : fpL);
+      f[v][4] = lw[v] ? fs[v][5] : (v > 0 ? fs[v - 1][4] : gpL);
+      f[v][2] = rw[v] ? fs[v][1] : (v < V - 1 ? fs[v + 1][2] : fmR);
+      f[v][5] = rw[v] ? fs[v][4] : (v < V - 1 ? fs[v + 1][5] : gmR);
+    }
+  }
+
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int local = threadIdx.x * V + v;
+    const long long pos = pos0 + v;
+    if (local >= halo && local < halo + bout && pos < N) {
+      R* dst = out + off + pos;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) dst[i * plane] = f[v][i];
     }
   }
 }
 
-template <typename R>
-cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, int B,
-                              long long ntiles, int K, int NT, const Consts<R>& c, cudaStream_t st,
-                              int grid_cap) {
-  if (ntiles <= 0) return cudaSuccess;
-  long long grid = ntiles;
-  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
-  switch (NT) {
-    case 256: step_tiles_kernel<R, 256><<<(unsigned)grid, 256, 0, st>>>(in, out, plane, lat, B, ntiles, K, c); break;
-    case 512: step_tiles_kernel<R, 512><<<(unsigned)grid, 512, 0, st>>>(in, out, plane, lat, B, ntiles, K, c); break;
-    case 1024: step_tiles_kernel<R, 1024><<<(unsigned)grid, 1024, 0, st>>>(in, out, plane, lat, B, ntiles, K, c); break;
-    default: return cudaErrorInvalidValue;
+// The same tile update for FP32 with two nodes per float2 lane (V = 2 or 4 nodes per thread), so
+// that the node arithmetic runs on Blackwell's paired FP32 instructions. Lane l of a thread holds
+// nodes 2l (x) and 2l + 1 (y).
+template <int NT, int V, bool CG>
+__device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
+                                                 long long start, int K, const Consts<float2>& c,
+                                                 float (*e_ut)[4], float (*e_f)[4]) {
+  constexpr int NW = NT / 32, NL = V / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int halo = 2 * K;
+  const int bout = NT * V - 2 * halo;
+  const long long off = d.offset, N = d.n;
+  const int bc = d.bc;
+  const float2 s_e = make_float2((float)d.s_e, (float)d.s_e), s_psi = make_float2((float)d.s_psi, (float)d.s_psi);
+  const float2 s_eps = make_float2((float)d.s_eps, (float)d.s_eps), q_src = make_float2((float)d.q_src, (float)d.q_src);
+  const float2 s0 = make_float2((float)d.s0, (float)d.s0);
+  const long long pos0 = start - halo + (long long)threadIdx.x * V;
+
+  float2 f[NL][6];
+  bool lw[V], rw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const long long pos = pos0 + v;
+    long long lp = pos;
+    if (bc == 0) {
+      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+    } else {
+      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+    }
+    lw[v] = (bc != 0) && pos == 0;
+    rw[v] = (bc != 0) && pos == N - 1;
+    const float* src = in + off + lp;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const float x = ld_state<float, CG>(src + i * plane);
+      if (v & 1) f[v >> 1][i].y = x; else f[v >> 1][i].x = x;
+    }
   }
+
+  for (int k = 0; k < K; ++k) {
+    Node<float2> m[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) node_state(f[l], c, s0, m[l]);
+    float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].T.y, 1);
+    float uR = __shfl_down_sync(0xffffffffu, m[0].u.x, 1), TR = __shfl_down_sync(0xffffffffu, m[0].T.x, 1);
+    if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].T.y; }
+    if (lane == 0) { e_ut[warp][2] = m[0].u.x; e_ut[warp][3] = m[0].T.x; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+
+    float2 fs[NL][6];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      float2 ul = make_float2(l > 0 ? m[l - 1].u.y : uL, m[l].u.x);
+      float2 Tl = make_float2(l > 0 ? m[l - 1].T.y : TL, m[l].T.x);
+      float2 ur = make_float2(m[l].u.y, l < NL - 1 ? m[l + 1].u.x : uR);
+      float2 Tr = make_float2(m[l].T.y, l < NL - 1 ? m[l + 1].T.x : TR);
+      if (lw[2 * l]) { ul.x = -m[l].u.x; Tl.x = m[l].T.x; }
+      if (lw[2 * l + 1]) { ul.y = -m[l].u.y; Tl.y = m[l].T.y; }
+      if (rw[2 * l]) { ur.x = -m[l].u.x; Tr.x = m[l].T.x; }
+      if (rw[2 * l + 1]) { ur.y = -m[l].u.y; Tr.y = m[l].T.y; }
+      node_collide(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0, c, fs[l]);
+    }
+    float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
+    float fmR = __shfl_down_sync(0xffffffffu, fs[0][2].x, 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5].x, 1);
+    if (lane == 31) { e_f[warp][0] = fs[NL - 1][1].y; e_f[warp][1] = fs[NL - 1][4].y; }
+    if (lane == 0) { e_f[warp][2] = fs[0][2].x; e_f[warp][3] = fs[0][5].x; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      f[l][0] = fs[l][0];
+      f[l][3] = fs[l][3];
+      // f+, g+ from the left node; f-, g- from the right node; walls reflect their own.
+      const float fpx = l > 0 ? fs[l - 1][1].y : fpL, gpx = l > 0 ? fs[l - 1][4].y : gpL;
+      const float fmy = l < NL - 1 ? fs[l + 1][2].x : fmR, gmy = l < NL - 1 ? fs[l + 1][5].x : gmR;
+      f[l][1] = make_float2(lw[2 * l] ? fs[l][2].x : fpx, lw[2 * l + 1] ? fs[l][2].y : fs[l][1].x);
+      f[l][4] = make_float2(lw[2 * l] ? fs[l][5].x : gpx, lw[2 * l + 1] ? fs[l][5].y : fs[l][4].x);
+      f[l][2] = make_float2(rw[2 * l] ? fs[l][1].x : fs[l][2].y, rw[2 * l + 1] ? fs[l][1].y : fmy);
+      f[l][5] = make_float2(rw[2 * l] ? fs[l][4].x : fs[l][5].y, rw[2 * l + 1] ? fs[l][4].y : gmy);
+    }
+  }
+
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int local = threadIdx.x * V + v;
+    const long long pos = pos0 + v;
+    if (local >= halo && local < halo + bout && pos < N) {
+      float* dst = out + off + pos;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) dst[i * plane] = (v & 1) ? f[v >> 1][i].y : f[v >> 1][i].x;
+    }
+  }
+}
+
+__device__ __forceinline__ int lattice_of_tile(const LatDev* lat, int B, long long tile) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {  // last lattice whose first tile is <= tile
+    const int mid = (lo + hi + 1) >> 1;
+    if (lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP32 with two or four nodes per thread runs on paired lanes; everything else on scalar lanes.
+template <typename R, int V>
+struct Lanes {
+  using type = R;
+};
+template <>
+struct Lanes<float, 2> {
+  using type = float2;
+};
+template <>
+struct Lanes<float, 4> {
+  using type = float2;
+};
+
+template <typename R, int NT, int V, bool CG>
+__device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
+                                            int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
+                                            R (*e_f)[4]) {
+  if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value)
+    tile_body_packed<NT, V, CG>(in, out, plane, d, start, K, c, e_ut, e_f);
+  else
+    tile_body<R, NT, V, CG>(in, out, plane, d, start, K, c, e_ut, e_f);
+}
+
+template <typename R, int NT, int V>
+__global__ void __launch_bounds__(NT) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
+                                                        long long plane, const LatDev* __restrict__ lat,
+                                                        int B, long long ntiles, int K,
+                                                        Consts<typename Lanes<R, V>::type> c) {
+  __shared__ R e_ut[NT / 32][4];
+  __shared__ R e_f[NT / 32][4];
+  const long long bout = NT * V - 4 * K;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int L = B > 1 ? lattice_of_tile(lat, B, tile) : 0;
+    const LatDev d = lat[L];
+    tile_update<R, NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+  }
+}
+
+template <typename R, int NT, int V>
+static cudaError_t launch_nt_v(const R* in, R* out, long long plane, const LatDev* lat, int B, long long ntiles,
+                               int K, const ConstSet<R>& cs, cudaStream_t st, long long grid) {
+  step_tiles_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, B, ntiles, K,
+                                                              cs.template get<typename Lanes<R, V>::type>());
   return cudaGetLastError();
 }
 
-template cudaError_t launch_step_tiles<float>(const float*, float*, long long, const LatDev*, int, long long,
-                                              int, int, const Consts<float>&, cudaStream_t, int);
+template <typename R>
+cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, int B, long long ntiles,
+                              int K, int NT, int V, const ConstSet<R>& c, cudaStream_t st, long long grid_cap) {
+  if (ntiles <= 0) return cudaSuccess;
+  long long grid = ntiles;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+#define LBM_CASE(nt, v) \
+  if (NT == nt && V == v) return launch_nt_v<R, nt, v>(in, out, plane, lat, B, ntiles, K, c, st, grid);
+  LBM_CASE(128, 1) LBM_CASE(128, 2) LBM_CASE(128, 4)
+  LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
+  LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
+  LBM_CASE(1024, 1)
+  if constexpr (sizeof(R) == 4) { LBM_CASE(1024, 2) }
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent launch over all time blocks. A work unit is (time block b of K steps, tile i); units
+// are claimed from a global counter in increasing order u = b * ntiles + i. Unit (b, i) reads buffer
+// b & 1 and writes buffer (b + 1) & 1, so it may start once tiles i - 1, i, i + 1 of its lattice have
+// finished block b - 1: that covers both its halo reads and the reads of the region it overwrites.
+// Every unit waits only on units with a smaller number, which were claimed earlier by CTAs that are
+// running, so the launch cannot deadlock whatever the number of resident CTAs. Each wait is bounded:
+// after spin_limit polls it sets the status word and the CTA stops; other CTAs see the status and
+// stop too, so the kernel always ends.
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename R, int NT, int V>
+__global__ void __launch_bounds__(NT) persistent_kernel(R* buf0, R* buf1, long long plane,
+                                                        const LatDev* __restrict__ lat, int B, long long ntiles,
+                                                        int K, long long nblocks, PersistentCtl ctl,
+                                                        Consts<typename Lanes<R, V>::type> c) {
+  __shared__ R e_ut[NT / 32][4];
+  __shared__ R e_f[NT / 32][4];
+  __shared__ long long s_unit;
+  __shared__ int s_go;
+  const long long total = nblocks * ntiles;
+  const long long bout = NT * V - 4 * K;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = (long long)atomicAdd(ctl.counter, 1ULL);
+      int go = u < total;
+      if (go && *((volatile int*)ctl.status) != 0) go = 0;
+      if (go && u >= ntiles) {
+        const long long b = u / ntiles, i = u % ntiles;
+        const int L = B > 1 ? lattice_of_tile(lat, B, i) : 0;
+        const long long t0 = lat[L].tile0;
+        const long long nt = (L + 1 < B ? lat[L + 1].tile0 : ntiles) - t0;
+        const long long li = i - t0;
+        const bool periodic = lat[L].bc == 0;
+        const long long left = li > 0 ? i - 1 : (periodic ? t0 + nt - 1 : i);
+        const long long right = li < nt - 1 ? i + 1 : (periodic ? t0 : i);
+        long long spins = 0;
+        for (;;) {
+          if (ld_acquire_gpu(ctl.done + left) >= b && ld_acquire_gpu(ctl.done + i) >= b &&
+              ld_acquire_gpu(ctl.done + right) >= b)
+            break;
+          if (*((volatile int*)ctl.status) != 0) { go = 0; break; }
+          if (++spins > ctl.spin_limit) { atomicExch(ctl.status, 1); go = 0; break; }
+          __nanosleep(100);
+        }
+      }
+      s_unit = u;
+      s_go = go;
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    if (!s_go) break;
+    const long long b = u / ntiles, i = u % ntiles;
+    const int L = B > 1 ? lattice_of_tile(lat, B, i) : 0;
+    const LatDev d = lat[L];
+    const bool withheld = (b == 0 && i == ctl.withhold);
+    if (!withheld)
+      tile_update<R, NT, V, true>((b & 1) ? buf1 : buf0, (b & 1) ? buf0 : buf1, plane, d, (i - d.tile0) * bout, K, c,
+                                  e_ut, e_f);
+    __syncthreads();
+    if (threadIdx.x == 0 && !withheld) {
+      __threadfence();
+      st_release_gpu(ctl.done + i, (int)(b + 1));
+    }
+  }
+}
+
+template <typename R, int NT, int V>
+static cudaError_t launch_persistent_nt_v(R* buf0, R* buf1, long long plane, const LatDev* lat, int B,
+                                          long long ntiles, int K, long long nblocks, const PersistentCtl& ctl,
+                                          const ConstSet<R>& cs, cudaStream_t st) {
+  const auto c = cs.template get<typename Lanes<R, V>::type>();
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, NT, V>, NT, 0);
+  long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
+  const long long total = nblocks * ntiles;
+  if (grid > total) grid = total;
+  persistent_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(buf0, buf1, plane, lat, B, ntiles, K, nblocks, ctl, c);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, int B, long long ntiles, int K,
+                              int NT, int V, long long nblocks, const PersistentCtl& ctl, const ConstSet<R>& c,
+                              cudaStream_t st) {
+  if (ntiles <= 0 || nblocks <= 0) return cudaSuccess;
+#define LBM_CASE(nt, v)       \
+  if (NT == nt && V == v) \
+    return launch_persistent_nt_v<R, nt, v>(buf0, buf1, plane, lat, B, ntiles, K, nblocks, ctl, c, st);
+  LBM_CASE(128, 1) LBM_CASE(128, 2) LBM_CASE(128, 4)
+  LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
+  LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
+  LBM_CASE(1024, 1)
+  if constexpr (sizeof(R) == 4) { LBM_CASE(1024, 2) }
+#undef LBM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_persistent<float>(float*, float*, long long, const LatDev*, int, long long, int, int, int,
+                                              long long, const PersistentCtl&, const ConstSet<float>&, cudaStream_t);
+template cudaError_t launch_persistent<double>(double*, double*, long long, const LatDev*, int, long long, int, int,
+                                               int, long long, const PersistentCtl&, const ConstSet<double>&,
+                                               cudaStream_t);
+
+bool valid_tile_config(int K, int NT, int V, bool fp64) {
+  const bool nt_ok = NT == 128 || NT == 256 || NT == 512 || NT == 1024;
+  const bool v_ok = V == 1 || V == 2 || V == 4;
+  const bool k_ok = K == 1 || K == 2 || K == 4 || K == 8;
+  // 1024 x 4 is not instantiated; FP64 1024 x 2 would spill at the 64-register cap of 1024 threads.
+  const bool size_ok = !(NT == 1024 && V == 4) && !(fp64 && NT == 1024 && V == 2);
+  return nt_ok && v_ok && k_ok && size_ok && NT * V - 4 * K >= 32;
+}
+
+template cudaError_t launch_step_tiles<float>(const float*, float*, long long, const LatDev*, int, long long, int,
+                                              int, int, const ConstSet<float>&, cudaStream_t, long long);
 template cudaError_t launch_step_tiles<double>(const double*, double*, long long, const LatDev*, int, long long,
-                                               int, int, const Consts<double>&, cudaStream_t, int);
+                                               int, int, int, const ConstSet<double>&, cudaStream_t, long long);
 
 }  // namespace lbm

@@ -33,6 +33,10 @@ LBM_BC_PERIODIC = 0
 LBM_BC_BOUNCEBACK = 1
 LBM_F64 = 0
 LBM_F32_SHIFTED = 1
+LBM_MODE_LAUNCH = 0
+LBM_MODE_PERSISTENT = 1
+LBM_MODE_PERSISTENT_GRAPH = 2
+MODES = {"launch": LBM_MODE_LAUNCH, "persistent": LBM_MODE_PERSISTENT, "graph": LBM_MODE_PERSISTENT_GRAPH}
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED}
 
 
@@ -93,12 +97,19 @@ def load_library(path: str = LIB_PATH):
             "lbm_get_populations": (i32, [vp, vp]),
             "lbm_set_populations": (i32, [vp, vp]),
             "lbm_diagnostics": (i32, [vp, P(d), P(i32)]),
-            "lbm_set_config": (i32, [vp, i32, i32]),
-            "lbm_get_config": (i32, [vp, P(i32), P(i32)]),
+            "lbm_set_config": (i32, [vp, i32, i32, i32]),
+            "lbm_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
             "lbm_autotune": (i32, [vp, i32]),
             "lbm_save": (i32, [vp, ctypes.c_char_p]),
             "lbm_load": (i32, [vp, ctypes.c_char_p]),
             "lbm_diagnostics_noalloc": (i32, [vp, i64, d, P(lbm_phys), vp, vp, vp]),
+            "lbm_set_mode": (i32, [vp, i32]),
+            "lbm_adjoint_forward": (i32, [vp, i64]),
+            "lbm_adjoint_backward": (i32, [vp, vp, vp, vp, vp, vp]),
+            "lbm_adjoint": (i32, [vp, i64, vp, vp, vp, vp, vp]),
+            "lbm_adjoint_release": (i32, [vp]),
+            "lbm_status": (i32, [vp]),
+            "lbm_debug_persistent": (i32, [vp, i64, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -288,13 +299,62 @@ class Lattice:
             self._check(rc, "lbm_diagnostics")
         return sums, flags, rc
 
-    def set_config(self, steps_per_launch: int = 0, block_threads: int = 0):
-        self._check(self.lib.lbm_set_config(self.ctx, int(steps_per_launch), int(block_threads)), "lbm_set_config")
+    def set_config(self, steps_per_launch: int = 0, block_threads: int = 0, nodes_per_thread: int = 0):
+        self._check(self.lib.lbm_set_config(self.ctx, int(steps_per_launch), int(block_threads),
+                                            int(nodes_per_thread)), "lbm_set_config")
 
     def get_config(self):
-        k, nt = ctypes.c_int32(), ctypes.c_int32()
-        self._check(self.lib.lbm_get_config(self.ctx, ctypes.byref(k), ctypes.byref(nt)), "lbm_get_config")
-        return k.value, nt.value
+        """(steps_per_launch, block_threads, nodes_per_thread)."""
+        k, nt, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm_get_config(self.ctx, ctypes.byref(k), ctypes.byref(nt), ctypes.byref(v)),
+                    "lbm_get_config")
+        return k.value, nt.value, v.value
+
+    # -- adjoint ---------------------------------------------------------------------------------
+    def adjoint_forward(self, T: int):
+        self._check(self.lib.lbm_adjoint_forward(self.ctx, int(T)), "lbm_adjoint_forward")
+
+    def adjoint_backward(self, dL_drho_T, want_fd0: bool = False, device: bool = False):
+        """Returns (dL/drho0 [N], dL/du0 [N], dL/drates [B, 2], dL/df0 [6, N] or None)."""
+        torch = _torch()
+        seed = _Arr(dL_drho_T, self.N)
+        if device:
+            out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(2)]
+            fd0 = torch.empty(6 * self.N, dtype=torch.float64, device="cuda") if want_fd0 else None
+        else:
+            out = [np.empty(self.N) for _ in range(2)]
+            fd0 = np.empty(6 * self.N) if want_fd0 else None
+        rates = np.empty(2 * self.B)
+        a = [_Arr(x, self.N, writable=True) for x in out]
+        f = None if fd0 is None else _Arr(fd0, 6 * self.N, writable=True)
+        self._check(self.lib.lbm_adjoint_backward(self.ctx, seed.ptr, a[0].ptr, a[1].ptr, rates.ctypes.data,
+                                                  None if f is None else f.ptr), "lbm_adjoint_backward")
+        return out[0], out[1], rates.reshape(self.B, 2), (None if fd0 is None else fd0.reshape(6, self.N))
+
+    def adjoint(self, T: int, rho_target):
+        """loss = sum (rho(T) - rho_target)^2 and its gradients: (loss, dL/drho0, dL/du0, dL/drates [B, 2])."""
+        tgt = _Arr(rho_target, self.N)
+        loss = np.zeros(1)
+        drho, du = np.empty(self.N), np.empty(self.N)
+        rates = np.empty(2 * self.B)
+        self._check(self.lib.lbm_adjoint(self.ctx, int(T), tgt.ptr, loss.ctypes.data, drho.ctypes.data,
+                                         du.ctypes.data, rates.ctypes.data), "lbm_adjoint")
+        return float(loss[0]), drho, du, rates.reshape(self.B, 2)
+
+    def adjoint_release(self):
+        self._check(self.lib.lbm_adjoint_release(self.ctx), "lbm_adjoint_release")
+
+    def set_mode(self, mode: str):
+        """"launch" (one kernel per k steps), "persistent" or "graph" (persistent, CUDA graph)."""
+        self._check(self.lib.lbm_set_mode(self.ctx, MODES[mode]), "lbm_set_mode")
+
+    def status(self) -> int:
+        """Synchronises; LBM_OK or LBM_ERR_TIMEOUT if a bounded wait of a persistent launch expired."""
+        return int(self.lib.lbm_status(self.ctx))
+
+    def debug_persistent(self, spin_limit: int = 20000000, withhold_tile: int = -1):
+        self._check(self.lib.lbm_debug_persistent(self.ctx, int(spin_limit), int(withhold_tile)),
+                    "lbm_debug_persistent")
 
     def autotune(self, trials: int = 3):
         self._check(self.lib.lbm_autotune(self.ctx, int(trials)), "lbm_autotune")

@@ -1,0 +1,149 @@
+"""The GPU adjoint (reverse mode through the C-ABI) against the oracle's forward-mode dual numbers
+and against central differences of the GPU forward run."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_02369_gb300 import build, lbm as L
+
+    build.build()
+    return L
+
+
+def _fields(N, seed, amp=0.03, bc=0):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * np.arange(N) / N
+    rho = 1.0 + sum(amp * rng.uniform(-1, 1) * np.sin(k * x + rng.uniform(0, 6.3)) for k in (1, 2, 3))
+    u = sum(amp * rng.uniform(-1, 1) * np.sin(k * x + rng.uniform(0, 6.3)) for k in (1, 2))
+    if bc:
+        u = u * np.sin(np.pi * (np.arange(N) + 0.5) / N)
+    s = -0.05 + sum(amp * rng.uniform(-1, 1) * np.cos(k * x + rng.uniform(0, 6.3)) for k in (1, 2))
+    return rho, u, s
+
+
+def _case():
+    lengths = np.array([40, 67, 33])
+    bc = np.array([0, 1, 0])
+    s_e = np.array([1.2, 1.5, 1.35])
+    data = [_fields(int(n), 31 + b, bc=int(bc[b])) for b, n in enumerate(lengths)]
+    targets = [_fields(int(n), 77 + b, amp=0.02)[0] for b, n in enumerate(lengths)]
+    return lengths, bc, s_e, data, targets
+
+
+def _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T, precision="f64"):
+    lat = lbm.Lattice(lengths, s_e=s_e, bc=bc, precision=precision)
+    lat.set_state_entropy(*[np.concatenate([d[k] for d in data]) for k in range(3)])
+    loss, drho, du, drates = lat.adjoint(T, np.concatenate(targets))
+    s_psi = None
+    lat.close()
+    return loss, drho, du, drates
+
+
+def test_adjoint_matches_oracle_dual_numbers(O, lbm):
+    """Directional derivatives of loss = sum (rho_T - rho*)^2 along random directions in
+    (rho0, u0, s_e, s_psi), per lattice (the loss is separable), FP64, within 1e-6 relative."""
+    T = 60
+    lengths, bc, s_e, data, targets = _case()
+    loss, drho, du, drates = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T)
+    off = np.r_[0, np.cumsum(lengths)]
+    rng = np.random.default_rng(5)
+    oracle_loss = 0.0
+    for b, n in enumerate(lengths):
+        ph = O.default_phys(bc=int(bc[b]))
+        rates = O.coupled_rates(s_e[b])
+        rho, u, s = data[b]
+        ndir = 4
+        vr = rng.standard_normal((ndir, n))
+        vu = rng.standard_normal((ndir, n))
+        vs = rng.standard_normal((ndir, 2))
+        vr[0] = 0.0; vu[0] = 0.0           # direction 0: rates only
+        vs[1] = 0.0                        # direction 1: fields only
+        fd, dfd = O.run_tangent(ph, rates, vs, rho, u, s, vr, vu, T, NTHREADS)
+        rho_T = O.moments(ph, fd)[:, 0]
+        oracle_loss += np.sum((rho_T - targets[b]) ** 2)
+        for k in range(ndir):
+            drho_T = ph.rho0 * dfd[k][:, :3].sum(axis=1)
+            d_oracle = np.sum(2 * (rho_T - targets[b]) * drho_T)
+            d_gpu = (np.dot(drho[off[b]:off[b + 1]], vr[k]) + np.dot(du[off[b]:off[b + 1]], vu[k])
+                     + np.dot(drates[b], vs[k]))
+            assert abs(d_gpu - d_oracle) <= 1e-6 * abs(d_oracle) + 1e-14, (b, k, d_gpu, d_oracle)
+    assert abs(loss - oracle_loss) <= 1e-12 * oracle_loss
+
+
+def test_adjoint_matches_central_differences_of_gpu_forward(lbm):
+    """Central differences (h = 1e-6) of the GPU's own forward loss along 3 probe directions."""
+    import torch
+
+    T = 45
+    lengths, bc, s_e, data, targets = _case()
+    rho0, u0, s0 = [np.concatenate([d[k] for d in data]) for k in range(3)]
+    tgt = np.concatenate(targets)
+    loss, drho, du, drates = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T)
+    rng = np.random.default_rng(8)
+
+    def L(r, v):
+        lat = lbm.Lattice(lengths, s_e=s_e, bc=bc)
+        lat.set_state_entropy(r, v, s0)
+        lat.step(T)
+        rt = lat.moments(device=False)[0]
+        lat.close()
+        return float(np.sum((rt - tgt) ** 2))
+
+    h = 1e-6
+    for _ in range(3):
+        vr, vu = rng.standard_normal(rho0.size), rng.standard_normal(rho0.size)
+        fdiff = (L(rho0 + h * vr, u0 + h * vu) - L(rho0 - h * vr, u0 - h * vu)) / (2 * h)
+        grad = np.dot(drho, vr) + np.dot(du, vu)
+        assert abs(grad - fdiff) <= 1e-6 * abs(grad) + 1e-12, (grad, fdiff)
+    torch.cuda.synchronize()
+
+
+def test_adjoint_fp32_close_to_fp64(lbm):
+    T = 60
+    lengths, bc, s_e, data, targets = _case()
+    l64, r64, u64, s64 = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T, "f64")
+    l32, r32, u32, s32 = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T, "f32")
+    assert abs(l32 - l64) <= 1e-4 * l64
+    for a, b in ((r32, r64), (u32, u64), (s32, s64)):
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+
+
+def test_autograd_function_matches_adjoint(lbm):
+    """torch.autograd.Function around the adjoint: gradients of sum((rho_T - rho*)^2)."""
+    import torch
+
+    from paper_1802_02369_gb300.autograd import lattice_run
+
+    T = 50
+    lengths, bc, s_e, data, targets = _case()
+    rho0, u0, s0 = [torch.from_numpy(np.concatenate([d[k] for d in data])).cuda() for k in range(3)]
+    rho0.requires_grad_(True)
+    u0.requires_grad_(True)
+    se_t = torch.tensor(s_e, dtype=torch.float64, requires_grad=True)
+    from oracle import coupled_rates
+    sp_t = torch.tensor([coupled_rates(x)[1] for x in s_e], dtype=torch.float64, requires_grad=True)
+    rho_T = lattice_run(rho0, u0, s0, se_t, sp_t, lengths, T, bc=bc)
+    tgt = torch.from_numpy(np.concatenate(targets)).cuda()
+    loss = ((rho_T - tgt) ** 2).sum()
+    loss.backward()
+    l2, drho, du, drates = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T)
+    assert abs(loss.item() - l2) <= 1e-12 * l2
+    np.testing.assert_allclose(rho0.grad.cpu().numpy(), drho, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(u0.grad.cpu().numpy(), du, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(se_t.grad.cpu().numpy(), drates[:, 0], rtol=1e-10)
+    np.testing.assert_allclose(sp_t.grad.cpu().numpy(), drates[:, 1], rtol=1e-10)

@@ -90,7 +90,7 @@ def test_small_and_ragged_sizes_fp64(O, lbm, N, bc):
     rho, u, p = smooth_data(N, seed=N + 7 * bc, bc=bc)
     ref = oracle_run(O, rho, u, p, 200, 1.3, bc=bc)
     outs = []
-    for cfg in [(1, 256), (2, 512), (4, 1024), (8, 256)]:
+    for cfg in [(1, 256, 1), (2, 512, 2), (4, 128, 4), (8, 256, 2), (4, 1024, 1)]:
         g = gpu_run(lbm, rho, u, p, 200, 1.3, bc=bc, config=cfg)
         assert rel_err(g, ref, scales()).max() <= 1e-12, cfg
         outs.append(np.stack(g))
@@ -263,3 +263,97 @@ def test_populations_roundtrip_and_autotune_keeps_result(O, lbm):
     ref = O.moments(ph, O.run(ph, O.coupled_rates(1.25), fd, 64))
     assert rel_err(lat.moments(device=False), ref, scales()).max() <= 1e-12
     lat.close()
+
+
+def _ragged(rng, B, nmax, s_range=(1.0, 1.4)):
+    lengths = rng.integers(3, nmax, B)
+    s_e = rng.uniform(*s_range, B)
+    bc = rng.integers(0, 2, B)
+    data = [smooth_data(int(n), seed=500 + b, amp=0.02, bc=int(bc[b])) for b, n in enumerate(lengths)]
+    fields = [np.concatenate([d[k] for d in data]) for k in range(3)]
+    return lengths, s_e, bc, fields
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_persistent_and_graph_modes_match_launch_mode(lbm, precision):
+    """One persistent launch over all time blocks (directly or replayed from a CUDA graph) gives
+    bitwise the same state as one launch per block; small tiles make many inter-tile waits."""
+    rng = np.random.default_rng(2024)
+    lengths, s_e, bc, fields = _ragged(rng, 37, 20000)
+    lengths[:2] = [3, 97]
+    lengths, fields = lengths, [np.concatenate([smooth_data(int(n), seed=900 + b, amp=0.02, bc=int(bc[b]))[k]
+                                                for b, n in enumerate(lengths)]) for k in range(3)]
+    results = {}
+    for mode in ("launch", "persistent", "graph"):
+        lat = lbm.Lattice(lengths, s_e=s_e, bc=bc, precision=precision)
+        lat.set_config(4, 128, 2)
+        lat.set_mode(mode)
+        lat.set_state(*fields)
+        for _ in range(3):              # 3 calls: new graph, new graph (other parity), cached graph
+            lat.step(103)               # 25 blocks of 4 steps + a 3-step remainder
+        assert lat.status() == lbm.LBM_OK
+        results[mode] = lat.populations()
+        lat.close()
+    assert np.array_equal(results["persistent"], results["launch"])
+    assert np.array_equal(results["graph"], results["launch"])
+
+
+@pytest.mark.parametrize("mode", ["persistent", "graph"])
+def test_persistent_wait_timeout_is_reported(lbm, mode):
+    """A tile whose first block is never released makes its neighbours' bounded waits expire: the
+    launch ends, lbm_status reports LBM_ERR_TIMEOUT, and the context keeps working."""
+    rng = np.random.default_rng(7)
+    lengths, s_e, bc, fields = _ragged(rng, 5, 6000)
+    lat = lbm.Lattice(lengths, s_e=s_e, bc=bc)
+    lat.set_config(2, 128, 1)
+    lat.set_mode(mode)
+    lat.set_state(*fields)
+    lat.debug_persistent(spin_limit=2000, withhold_tile=1)
+    lat.step(8)
+    assert lat.status() == lbm.LBM_ERR_TIMEOUT
+    assert lat.status() == lbm.LBM_OK      # cleared
+    lat.debug_persistent(withhold_tile=-1)
+    lat.set_state(*fields)
+    lat.step(8)
+    assert lat.status() == lbm.LBM_OK
+    got = lat.populations()
+    lat.close()
+    ref = lbm.Lattice(lengths, s_e=s_e, bc=bc)
+    ref.set_config(2, 128, 1)
+    ref.set_state(*fields)
+    ref.step(8)
+    assert np.array_equal(got, ref.populations())
+    ref.close()
+
+
+def test_riemann_batch_fp32_against_oracle(O, lbm):
+    """A seeded subset of the ragged Riemann batch (lengths capped for the oracle), FP32, persistent
+    graph mode, 2000 steps: lattices the oracle keeps stable agree to L1(rho) <= 1e-4, and lattices
+    on which the oracle blows up are flagged by the GPU diagnostics as well."""
+    ph = O.default_phys()
+    bat = W.ragged_batch(8, 1802, ph.p0, n_min=512, n_max=4096)
+    lat = lbm.Lattice(bat.lengths, s_e=bat.s_e, bc=bat.bc, precision="f32")
+    lat.set_mode("graph")
+    lat.set_state(bat.rho, bat.u, bat.p)
+    lat.autotune(1)
+    lat.set_state(bat.rho, bat.u, bat.p)
+    lat.step(2000)
+    assert lat.status() == lbm.LBM_OK
+    rho_gpu = np.asarray(lat.moments(device=False)[0])
+    _, flags, _ = lat.diagnostics()
+    lat.close()
+    stable = 0
+    for b in range(8):
+        phb = O.default_phys(bc=int(bat.bc[b]))
+        r, u, p = bat.lattice(b)
+        fd = O.run(phb, O.coupled_rates(bat.s_e[b]), O.init(phb, r, u, p=p), 2000, NTHREADS)
+        _, oflag = O.diagnostics(phb, fd)
+        if oflag == 0:
+            stable += 1
+            ref = O.moments(phb, fd)[:, 0]
+            got = rho_gpu[bat.offsets[b]:bat.offsets[b + 1]]
+            assert flags[b] == 0
+            assert np.mean(np.abs(got - ref)) <= 1e-4, b
+        else:
+            assert flags[b] != 0, b
+    assert stable >= 1
