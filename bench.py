@@ -32,6 +32,11 @@ AMP = 0.1
 # Algorithmic bytes per node-update: the six populations read and written once (FP32 / FP64).
 BYTES_PER_NODE = {"f32": 48, "f64": 96}
 WORKLOAD = "steepening acoustic wave, single periodic lattice N=2^26, lambda=1, s_e=1.2"
+# DRAM bytes per node per launch of the step kernel, measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the same workload at N = 2^23 and scaled to a full launch by the node
+# count (traffic is proportional to the nodes); keyed by (precision, k, block_threads,
+# nodes_per_thread) of the current kernel version. Summaries: profiles/step_tiles_*.md.
+TRAFFIC_BYTES_PER_NODE = {("f32", 8, 256, 2): (201.381632e6 + 149.676544e6) / 8388608}
 
 
 def measured_peaks():
@@ -190,6 +195,85 @@ def time_device(lat, torch, steps: int, warmup: int, dist, world: int):
     return ms
 
 
+def run_batched(args, lbm, torch, hbm_peak, world):
+    """Ragged batch of independent Riemann problems (4096 lattices, lengths U[512, 65536], s_e
+    U[1.0, 1.9], pressures in units of p0, periodic or bounce-back), FP32, one persistent launch
+    replayed from a CUDA graph."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    bat = W.ragged_batch(4096, 1802, W.reference_pressure())
+    ntot = int(bat.offsets[-1])
+    fields = [torch.from_numpy(x).cuda() for x in (bat.rho, bat.u, bat.p)]
+    lat = lbm.Lattice(bat.lengths, s_e=bat.s_e, bc=bat.bc, precision="f32")
+    lat.set_state(*fields)
+    k, nt, vpt = lat.autotune(1)
+    lat.set_mode("graph")
+    steps = (args.batched_steps // k) * k
+    lat.set_state(*fields)
+    lat.step(steps)                       # captures the graph and warms up
+    lat.set_state(*fields)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)                       # one graph replay: one persistent launch
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = lat.status()
+    _, flags, _ = lat.diagnostics()
+    lat.close()
+    del fields
+    torch.cuda.empty_cache()
+    glups = world * ntot * steps / (ms * 1e-3) / 1e9
+    alg = ntot * BYTES_PER_NODE["f32"] * (steps // k)   # one state read + write per block of k steps
+    achieved = alg / (ms * 1e-3) / 1e9
+    return {"value": glups, "unit": UNIT, "lattices": 4096, "nodes": ntot, "steps": steps, "ms": ms,
+            "steps_per_launch_block": k, "block_threads": nt, "nodes_per_thread": vpt, "launches": 1,
+            "mode": "persistent kernel replayed from a CUDA graph", "status": status,
+            "lattices_flagged_unstable": int((flags != 0).sum()),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "effective_gbs": glups / world * BYTES_PER_NODE["f32"],
+                         "effective_frac": glups / world * BYTES_PER_NODE["f32"] / hbm_peak}}
+
+
+def run_adjoint(args, lbm, torch):
+    """Gradient of sum (rho_T - rho*)^2 for 256 lattices of 65536 nodes (Gaussian density bumps,
+    seed 2369; target from seed 2370), sqrt(T) checkpointing. Reported: node-steps of the
+    differentiated run per second, over forward + backward."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    B, N = 256, 65536
+    out = {}
+    for prec, T in (("f32", args.adjoint_steps_f32), ("f64", args.adjoint_steps_f64)):
+        rho, u, p = W.gaussian_bumps(B, N, 2369, W.reference_pressure())
+        rho_t, u_t, p_t = W.gaussian_bumps(B, N, 2370, W.reference_pressure())
+        tgt_lat = lbm.Lattice(np.full(B, N), s_e=1.5, precision=prec)
+        tgt_lat.set_state(rho_t.ravel(), u_t.ravel(), p_t.ravel())
+        tgt_lat.step(T)
+        target = tgt_lat.moments(device=True)[0]
+        tgt_lat.close()
+        lat = lbm.Lattice(np.full(B, N), s_e=1.5, precision=prec)
+        d = [torch.from_numpy(x.ravel()).cuda() for x in (rho, u, p)]
+        lat.set_state(*d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.adjoint_forward(T)
+        rho_T = lat.moments(device=True)[0]
+        seed = 2.0 * (rho_T - target)
+        g_rho, g_u, g_rates, _ = lat.adjoint_backward(seed, device=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        lat.adjoint_release()
+        lat.close()
+        del d, target, rho_T, seed, g_rho, g_u
+        torch.cuda.empty_cache()
+        out[prec] = {"value": B * N * T / dt / 1e9, "unit": "GLUPS (differentiated node-steps / s)", "T": T,
+                     "lattices": B, "N": N, "seconds": dt, "checkpoint_segment": int(round(T ** 0.5)),
+                     "dL_dse_first_lattice": float(g_rates[0, 0])}
+    return out
+
+
 def run_ours(args, rank: int, world: int, local: int, dist):
     import torch
 
@@ -260,6 +344,9 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     e2e = {"value": world * N_NODES * K / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 3 * 8 * N_NODES / K, "d2h_bytes_per_step": 3 * 8 * N_NODES / K}
 
+    batched = None if args.no_batched else run_batched(args, lbm, torch, hbm_peak, world)
+    adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch)
+
     if rank != 0:
         return
     cpu = None
@@ -273,8 +360,9 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                "sample": f"first 2^22 nodes of the workload (periodic), {st} steps, {dt:.1f} s, FP64"}
 
     def roof(r, prec):
+        tb = TRAFFIC_BYTES_PER_NODE.get((prec, r["k"], r["block_threads"], r["nodes_per_thread"]))
         return {"bound": "hbm", "achieved": r["achieved"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": r["achieved"] / hbm_peak, "traffic": None,
+                "frac": r["achieved"] / hbm_peak, "traffic": None if tb is None else tb * N_NODES,
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": N_NODES * BYTES_PER_NODE[prec],
                 "steps_per_launch": r["k"], "launch_ms": r["launch_ms"],
@@ -291,7 +379,9 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof(f32, "f32"),
             "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
-                     "roofline": roof(f64, "f64")},
+                     "steps_per_launch": f64["k"], "block_threads": f64["block_threads"],
+                     "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof(f64, "f64")},
+            "batched_fp32": batched, "adjoint": adjoint,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
     print(json.dumps(line), flush=True)
@@ -309,6 +399,11 @@ def main():
     ap.add_argument("--precisions", default="f32,f64")
     ap.add_argument("--config", default="", help="k,block_threads,nodes_per_thread instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-steps-f32", type=int, default=4000)
+    ap.add_argument("--adjoint-steps-f64", type=int, default=1000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -158,6 +158,12 @@ int lbm_status(lbm_ctx *ctx);
  * is computed but never released, so that its neighbours' waits must expire (-1: none). */
 int lbm_debug_persistent(lbm_ctx *ctx, int64_t spin_limit, int64_t withhold_tile);
 
+/* Test hook: applies one of the FP32 functions of the node update elementwise to n floats
+ * (device pointers x -> y, enqueued on stream): fn 0 = log(1+x) as evaluated on paired lanes,
+ * 1 = log(1+x) on single lanes (CUDA's log1pf), 2 = exp(x)-1 on paired lanes, 3 = exp(x)-1 on
+ * single lanes (CUDA's expm1f), 4 = the FP32 reciprocal. */
+int lbm_debug_eval_f32(const float *x, float *y, int64_t n, int32_t fn, void *stream);
+
 /* Times every valid (k, block_threads, nodes_per_thread) on the current state (which is left
  * unchanged; each trial writes only the second buffer, over at most 16384 tiles) and keeps the
  * fastest per node-update. trials >= 1 timed launches per candidate. Synchronises. Needs a state. */

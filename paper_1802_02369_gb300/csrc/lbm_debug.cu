@@ -1,0 +1,31 @@
+// Test hook: evaluates the FP32 lane functions of the node update on device arrays, so that the
+// series used on paired lanes can be checked against CUDA's own functions and against FP64.
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+namespace {
+
+__global__ void eval_kernel(const float* __restrict__ x, float* __restrict__ y, long long n, int fn) {
+  const long long i = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float2 a = make_float2(x[i], i + 1 < n ? x[i + 1] : 0.0f);
+  float2 r;
+  switch (fn) {
+    case 0: r = lbm::m_log1p(a); break;                                   // paired-lane log1p
+    case 1: r = make_float2(lbm::m_log1p(a.x), lbm::m_log1p(a.y)); break;  // CUDA log1pf
+    case 2: r = lbm::m_expm1(a); break;                                   // paired-lane expm1
+    case 3: r = make_float2(lbm::m_expm1(a.x), lbm::m_expm1(a.y)); break;  // CUDA expm1f
+    default: r = lbm::m_rcp(a); break;                                    // reciprocal
+  }
+  y[i] = r.x;
+  if (i + 1 < n) y[i + 1] = r.y;
+}
+
+}  // namespace
+
+extern "C" int lbm_debug_eval_f32(const float* x, float* y, int64_t n, int32_t fn, void* stream) {
+  if (!x || !y || n < 1 || fn < 0 || fn > 4) return LBM_ERR_INVALID_ARG;
+  const long long pairs = (n + 1) / 2;
+  eval_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, fn);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}

@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
             "lbm_load": (i32, [vp, ctypes.c_char_p]),
             "lbm_diagnostics_noalloc": (i32, [vp, i64, d, P(lbm_phys), vp, vp, vp]),
             "lbm_set_mode": (i32, [vp, i32]),
+            "lbm_debug_eval_f32": (i32, [vp, vp, i64, i32, vp]),
             "lbm_adjoint_forward": (i32, [vp, i64]),
             "lbm_adjoint_backward": (i32, [vp, vp, vp, vp, vp, vp]),
             "lbm_adjoint": (i32, [vp, i64, vp, vp, vp, vp, vp]),
