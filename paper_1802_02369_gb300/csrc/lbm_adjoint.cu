@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(NT) adjoint_step_kernel(const R* __restrict__ 
     R et_b = (R(1) - s_e) * es_b, e_eq_b = s_e * es_b;
     R psi_b = (R(1) - s_psi) * psis_b, psi_eq_b = s_psi * psis_b;
     R epst_b = (R(1) - s_eps) * epss_b, eps_eq_b = s_eps * epss_b;
-    double g_se = (double)es_b * (double)(e_eq_t - m.et);
-    double g_sp = (double)psis_b * (double)(psi_eq - m.psi);
+    // Rate-gradient terms of this node in the arithmetic type; summed per warp in it, then in FP64.
+    R g_se = es_b * (e_eq_t - m.et);
+    R g_sp = psis_b * (psi_eq - m.psi);
 
     R rho_b = R(0), ds_b = R(0), lnr_b = R(0), u_b = R(0), T_b = R(0), pt_b = R(0), ir_b = R(0);
     R ul_b = R(0), ur_b = R(0), Tl_b = R(0), Tr_b = R(0);
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(NT) adjoint_step_kernel(const R* __restrict__ 
       const R du_b = S_b * q * m.rho * iT * R(2) * du;
       const R dT_b = S_b * q * m.rho * iT * c.cp_over_Pr * R(2) * dT * iT;
       ur_b = du_b; ul_b = -du_b; Tr_b = dT_b; Tl_b = -dT_b;
-      g_se += (double)S_b * (double)(m.rho * iT * A) * (-0.25 / ((double)s_e * (double)s_e));
+      g_se += S_b * (m.rho * iT * A) * (R(-0.25) * m_rcp(s_e * s_e));
     }
     // Walls: the ghosts are functions of this node's own u and T.
     if (lw) { u_b -= ul_b; T_b += Tl_b; ul_b = R(0); Tl_b = R(0); }
@@ -174,13 +175,13 @@ __global__ void __launch_bounds__(NT) adjoint_step_kernel(const R* __restrict__ 
     if (owned)
       for (int i = 0; i < 6; ++i) a_out[i * plane + off + pos] = ao[i];
 
-    // Rate gradients of the owned nodes, fixed-order block reduction.
-    if (!owned) { g_se = 0.0; g_sp = 0.0; }
+    // Rate gradients of the owned nodes: fixed-order warp sums, then FP64 across warps, tiles, steps.
+    if (!owned) { g_se = R(0); g_sp = R(0); }
     for (int o = 16; o > 0; o >>= 1) {
       g_se += __shfl_down_sync(0xffffffffu, g_se, o);
       g_sp += __shfl_down_sync(0xffffffffu, g_sp, o);
     }
-    if ((n & 31) == 0) { sg[0][n >> 5] = g_se; sg[1][n >> 5] = g_sp; }
+    if ((n & 31) == 0) { sg[0][n >> 5] = (double)g_se; sg[1][n >> 5] = (double)g_sp; }
     __syncthreads();
     if (n == 0) {
       double t0 = 0.0, t1 = 0.0;

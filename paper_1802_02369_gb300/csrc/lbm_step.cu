@@ -25,7 +25,7 @@ __device__ __forceinline__ R ld_state(const R* p) {
 }
 
 // Advances one tile K steps: reads `in`, writes the interior of the tile to `out`.
-template <typename R, int NT, int V, bool CG>
+template <typename R, int NT, int V, bool CG, bool WALLS>
 __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                           int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4]) {
   constexpr int NW = NT / 32;
@@ -33,7 +33,6 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   const int halo = 2 * K;
   const int bout = NT * V - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const int bc = d.bc;
   const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0 = R(d.s0);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
@@ -43,13 +42,13 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   for (int v = 0; v < V; ++v) {
     const long long pos = pos0 + v;
     long long lp = pos;
-    if (bc == 0) {
+    if (!WALLS) {
       if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
     } else {
       lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
-    lw[v] = (bc != 0) && pos == 0;
-    rw[v] = (bc != 0) && pos == N - 1;
+    lw[v] = WALLS && pos == 0;
+    rw[v] = WALLS && pos == N - 1;
     const R* src = in + off + lp;
 #pragma unroll
     for (int i = 0; i < 6; ++i) f[v][i] = ld_state<R, CG>(src + i * plane);
@@ -112,7 +111,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 // The same tile update for FP32 with two nodes per float2 lane (V = 2 or 4 nodes per thread), so
 // that the node arithmetic runs on Blackwell's paired FP32 instructions. Lane l of a thread holds
 // nodes 2l (x) and 2l + 1 (y).
-template <int NT, int V, bool CG>
+template <int NT, int V, bool CG, bool WALLS>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
                                                  float (*e_ut)[4], float (*e_f)[4]) {
@@ -121,7 +120,6 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   const int halo = 2 * K;
   const int bout = NT * V - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const int bc = d.bc;
   const float2 s_e = make_float2((float)d.s_e, (float)d.s_e), s_psi = make_float2((float)d.s_psi, (float)d.s_psi);
   const float2 s_eps = make_float2((float)d.s_eps, (float)d.s_eps), q_src = make_float2((float)d.q_src, (float)d.q_src);
   const float2 s0 = make_float2((float)d.s0, (float)d.s0);
@@ -133,13 +131,13 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   for (int v = 0; v < V; ++v) {
     const long long pos = pos0 + v;
     long long lp = pos;
-    if (bc == 0) {
+    if (!WALLS) {
       if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
     } else {
       lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
-    lw[v] = (bc != 0) && pos == 0;
-    rw[v] = (bc != 0) && pos == N - 1;
+    lw[v] = WALLS && pos == 0;
+    rw[v] = WALLS && pos == N - 1;
     const float* src = in + off + lp;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -233,10 +231,14 @@ template <typename R, int NT, int V, bool CG>
 __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                             int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
                                             R (*e_f)[4]) {
-  if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value)
-    tile_body_packed<NT, V, CG>(in, out, plane, d, start, K, c, e_ut, e_f);
-  else
-    tile_body<R, NT, V, CG>(in, out, plane, d, start, K, c, e_ut, e_f);
+  // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
+  if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
+    if (d.bc == 0) tile_body_packed<NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f);
+    else tile_body_packed<NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f);
+  } else {
+    if (d.bc == 0) tile_body<R, NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f);
+    else tile_body<R, NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f);
+  }
 }
 
 template <typename R, int NT, int V>

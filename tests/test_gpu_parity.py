@@ -363,29 +363,32 @@ def test_precision_sweep_amplitude_02(O, lbm):
     """Steepening waves of amplitude 0.2 (rho = 1 + 0.2 sin, u = 0.2 sin) with s_e in {1.2, 1.6, 1.9}
     (lattice b takes s_e[b mod 3]), FP32 shifted populations against FP64 and the oracle. The
     scheme is linearly unstable at |u| = 0.2 (spectral radius 1.05-1.15 at grid scale), so both
-    precisions and the oracle must blow up from rounding noise; before that (100 steps) FP64
-    matches the oracle to 1e-12, FP32 to 1e-5, and mass and momentum are conserved per step."""
+    precisions and the oracle must blow up from rounding noise. The instability also amplifies
+    rounding differences (about 1.15^n after n steps), so parity is checked after 40 steps (a
+    factor of at most about 270): FP64 matches the oracle to 1e-12, FP32 to 1e-5, and mass and
+    momentum are conserved per step; by step 1000 every lattice is flagged."""
     ph = O.default_phys()
     N, B = 1 << 16, 6
     s_vals = np.array([1.2, 1.6, 1.9])
     s_e = s_vals[np.arange(B) % 3]
     rho, u, p = W.steepening_wave(N, 0.2, ph.p0)
     fields = [np.tile(x, B) for x in (rho, u, p)]
-    refs = {se: oracle_run(O, rho, u, p, 100, se) for se in s_vals}
+    n_par = 40
+    refs = {se: oracle_run(O, rho, u, p, n_par, se) for se in s_vals}
     for precision, tol, drift_tol in (("f64", 1e-12, 1e-15), ("f32", 1e-5, 1e-8)):
         lat = lbm.Lattice(np.full(B, N), s_e=s_e, precision=precision)
         lat.set_state(*fields)
         sums0, _, _ = lat.diagnostics()
-        lat.step(100)
+        lat.step(n_par)
         sums, flags, rc = lat.diagnostics()
         assert rc == lbm.LBM_OK
         g = np.stack(lat.moments(device=False), axis=1)
         for b in range(B):
             gb = g[b * N:(b + 1) * N]
             assert rel_err(list(gb.T), refs[s_e[b]], scales()).max() <= tol, (precision, b)
-        drift = np.abs(sums[:, :2] - sums0[:, :2]).max(axis=0) / (100 * sums0[:, 0].max())
+        drift = np.abs(sums[:, :2] - sums0[:, :2]).max(axis=0) / (n_par * sums0[:, 0].max())
         assert drift.max() <= drift_tol, (precision, drift)
-        lat.step(900)
+        lat.step(1000 - n_par)
         _, flags, rc = lat.diagnostics()
         assert rc == lbm.LBM_ERR_UNSTABLE and np.all(flags != 0), (precision, flags)
         lat.close()
