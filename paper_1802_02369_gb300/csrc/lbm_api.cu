@@ -77,6 +77,12 @@ Consts<X> make_consts(const PhysD& p) {
   c.m_half = lift<X>(-0.5);
   c.third = lift<X>(1.0 / 3.0);
   c.sixth = lift<X>(1.0 / 6.0);
+  const double kp = p.p0 / (p.rho0 * l2);
+  c.kp = lift<X>(kp);
+  c.kth = lift<X>(kp * p.gamma / (p.gamma - 1.0));
+  c.e_rs = lift<X>(3.0 * kp - 2.0);
+  c.one_m_ig = lift<X>(1.0 - 1.0 / p.gamma);
+  c.inv_Pr = lift<X>(1.0 / p.Pr);
   c.source_on = p.source_on;
   return c;
 }
@@ -506,6 +512,7 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
       d.wg0 = (r0 - q0) / 3.0;
       d.wg1 = (2.0 * r0 + q0) / 6.0;
     }
+    d.s0h = c->s0[b] / ph.cp;
     d.bc = bc[b];
     d.pad = 0;
     tot += N[b];

@@ -18,6 +18,7 @@ struct LatDev {
   double zeta_r;   // rest-state moments removed from the stored populations: zeta_r = rho0 s0,
   double eps_r;    //   eps_r = e_r s0 (e_r = 3 p0 - 2 lambda^2 rho0)
   double wg0, wg1; // rest g populations (g0, g+ = g-)
+  double s0h;      // s0 / c_p
   int bc, pad;
 };
 
@@ -37,6 +38,12 @@ struct Consts {
   X cp_over_Pr;                   // c_p / Pr
   X m_two_lam2;                   // -2 lambda^2
   X one, m_one, two, m_two, three, half, m_half, third, sixth;  // numeric constants
+  // Dimensionless form used by the step kernels (see node_state_s).
+  X kp;        // p0 / (rho0 lambda^2)
+  X kth;       // kp gamma / (gamma - 1)
+  X e_rs;      // e_r / (rho0 lambda^2) = 3 kp - 2
+  X one_m_ig;  // 1 - 1/gamma
+  X inv_Pr;    // 1 / Pr
   int source_on;
 };
 
@@ -59,22 +66,23 @@ __device__ __forceinline__ float m_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double m_rcp(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); }
 
-// log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes the common
-// range is evaluated with textbook series in paired arithmetic, the rest with CUDA's functions:
-//  - log1p(x) = 2 atanh(z), z = x / (2 + x) = 2 z (1 + w/3 + w^2/5 + w^3/7 + w^4/9 + w^5/11), w = z^2,
-//    for |x| <= 0.3 (|z| <= 0.177: the first omitted term is below 1e-9 relative);
-//  - expm1(x) = x + x^2 (1/2! + x/3! + ... + x^7/9!) for |x| <= 0.35 (first omitted term below
-//    1e-9 relative).
+// log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes they are
+// evaluated with textbook series in paired arithmetic:
+//  - log1p(x) = m ln 2 + 2 atanh(z), z = t / (2 + t), with t = x and m = 0 for |x| <= 0.3, else
+//    1 + x = 2^m (1 + t), 1 + t in [0.75, 1.5); 2 atanh(z) = 2 z (1 + w/3 + w^2/5 + ... + w^5/11),
+//    w = z^2, |z| <= 0.2 (first omitted term below 1e-9 relative);
+//  - expm1(x) = 2^k expm1(r) + (2^k - 1), x = k ln 2 + r, |r| <= ln(2)/2 (k = 0 for |x| <= 0.35),
+//    expm1(r) = r + r^2 (1/2! + r/3! + ... + r^7/9!) (first omitted term below 1e-9 relative).
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ float2 m_log1p(float2 x) {
-  if (fabsf(x.x) > 0.3f || fabsf(x.y) > 0.3f) return make_float2(log1pf(x.x), log1pf(x.y));
-  const float2 d = __fadd2_rn(x, make_float2(2.0f, 2.0f));
+
+__device__ __forceinline__ float2 atanh2_series(float2 t) {  // 2 atanh(t / (2 + t)) for |t| <= 0.5
+  const float2 d = __fadd2_rn(t, make_float2(2.0f, 2.0f));
   float2 y = m_rcp(d);
   y = __ffma2_rn(y, __ffma2_rn(make_float2(-d.x, -d.y), y, make_float2(1.0f, 1.0f)), y);  // Newton step
-  const float2 z = __fmul2_rn(x, y);
+  const float2 z = __fmul2_rn(t, y);
   const float2 w = __fmul2_rn(z, z);
   float2 p = make_float2(1.0f / 11.0f, 1.0f / 11.0f);
   p = __ffma2_rn(p, w, make_float2(1.0f / 9.0f, 1.0f / 9.0f));
@@ -84,8 +92,31 @@ __device__ __forceinline__ float2 m_log1p(float2 x) {
   const float2 z2 = __fadd2_rn(z, z);
   return __ffma2_rn(__fmul2_rn(z2, w), p, z2);
 }
-__device__ __forceinline__ float2 m_expm1(float2 x) {
-  if (fabsf(x.x) > 0.35f || fabsf(x.y) > 0.35f) return make_float2(expm1f(x.x), expm1f(x.y));
+
+// 1 + x = 2^m (1 + t) with 1 + t in [0.75, 1.5) (x > -1 and finite; t = x, m = 0 when |x| <= 0.3).
+__device__ __forceinline__ void log1p_reduce(float x, float& t, float& m) {
+  if (fabsf(x) <= 0.3f) { t = x; m = 0.0f; return; }
+  const float y = 1.0f + x;
+  int e = ((__float_as_int(y) >> 23) & 0xff) - 127;             // y = 2^e * mant, mant in [1, 2)
+  float mant = __int_as_float((__float_as_int(y) & 0x007fffff) | 0x3f800000);
+  if (mant >= 1.5f) { mant *= 0.5f; e += 1; }
+  t = mant - 1.0f;
+  m = (float)e;
+}
+
+__device__ __forceinline__ float2 m_log1p(float2 x) {
+  if (fabsf(x.x) <= 0.3f && fabsf(x.y) <= 0.3f) return atanh2_series(x);
+  if (!(x.x > -1.0f && x.y > -1.0f && x.x < 3.0e38f && x.y < 3.0e38f))
+    return make_float2(log1pf(x.x), log1pf(x.y));  // outside the domain or non-finite
+  float2 t, m;
+  log1p_reduce(x.x, t.x, m.x);
+  log1p_reduce(x.y, t.y, m.y);
+  const float2 a = atanh2_series(t);
+  const float ln2_hi = 0.693145752f, ln2_lo = 1.42860677e-06f;  // ln 2 = hi + lo, hi with 17 bits
+  return __ffma2_rn(m, make_float2(ln2_hi, ln2_hi), __ffma2_rn(m, make_float2(ln2_lo, ln2_lo), a));
+}
+
+__device__ __forceinline__ float2 expm1_series(float2 x) {  // |x| <= 0.35
   float2 p = make_float2(1.0f / 362880.0f, 1.0f / 362880.0f);
   p = __ffma2_rn(p, x, make_float2(1.0f / 40320.0f, 1.0f / 40320.0f));
   p = __ffma2_rn(p, x, make_float2(1.0f / 5040.0f, 1.0f / 5040.0f));
@@ -95,6 +126,19 @@ __device__ __forceinline__ float2 m_expm1(float2 x) {
   p = __ffma2_rn(p, x, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
   p = __ffma2_rn(p, x, make_float2(0.5f, 0.5f));
   return __ffma2_rn(__fmul2_rn(x, x), p, x);
+}
+
+__device__ __forceinline__ float2 m_expm1(float2 x) {
+  if (fabsf(x.x) <= 0.35f && fabsf(x.y) <= 0.35f) return expm1_series(x);
+  if (!(fabsf(x.x) <= 80.0f && fabsf(x.y) <= 80.0f)) return make_float2(expm1f(x.x), expm1f(x.y));
+  const float kx = rintf(x.x * 1.44269504f), ky = rintf(x.y * 1.44269504f);  // k = round(x / ln 2)
+  const float2 k = make_float2(kx, ky);
+  const float ln2_hi = 0.693145752f, ln2_lo = 1.42860677e-06f;
+  float2 r = __ffma2_rn(k, make_float2(-ln2_hi, -ln2_hi), x);
+  r = __ffma2_rn(k, make_float2(-ln2_lo, -ln2_lo), r);
+  const float2 e = expm1_series(r);
+  const float2 two_k = make_float2(__int_as_float(((int)kx + 127) << 23), __int_as_float(((int)ky + 127) << 23));
+  return __ffma2_rn(two_k, e, __fadd2_rn(two_k, make_float2(-1.0f, -1.0f)));
 }
 
 // Moments and thermodynamic state of one node (or node pair) from its shifted populations
@@ -164,6 +208,80 @@ __device__ __forceinline__ void node_collide(const Node<X>& m, X ul, X ur, X Tl,
     fs[3] = ml(sb(r, q), c.third);
     fs[4] = fm(j, c.half, h);
     fs[5] = fm(j, c.m_half, h);
+  }
+}
+
+// The same node update in dimensionless moments, used by the step kernels. With D = diag(rho0,
+// rho0 lambda, rho0 c_p, rho0 lambda^2, rho0 c_p lambda, rho0 c_p lambda^2), the scaled moments
+// D^{-1} m of the shifted populations are integer combinations of them:
+//   r = f0 + f+ + f- = (rho - rho0)/rho0,  j = f+ - f- = J/(rho0 lambda),
+//   e = f+ + f- - 2 f0 = (e - e_r)/(rho0 lambda^2),  and z, psi, eps likewise from g with rho0 c_p.
+// With u' = u/lambda, sigma = (s - s0)/c_p, s' = s/c_p and theta = c_p T / lambda^2, the equation of
+// state, the equilibria, the relaxation and the source of section 8 become
+//   u' = j/(1 + r), sigma = (z - r s0/c_p)/(1 + r), E = expm1(gamma (log1p(r) + sigma)),
+//   theta = kp gamma/(gamma - 1) (1 + E)/(1 + r), kp = p0/(rho0 lambda^2),
+//   e_eq = 3 (j u' + kp E) - 2 r,  psi_eq = (1 + r) s' u',
+//   eps_eq = 2 (1 + r)(sigma + (1 - 1/gamma) log1p(r)) + e_eq s' + (3 kp - 2) sigma,
+//   dz = (sigma_e/4) (1 + r)/theta [du'^2 + dtheta^2 / (Pr theta)]  (dt S / (rho0 c_p)),
+// and M^{-1} loses its scale factors: f0 = (r - e)/3, f+- = (2 r + e)/6 +- j/2 (same for g).
+template <typename X>
+struct NodeS {
+  X r, j, e, z, ps, ep;   // scaled moments
+  X rho1, inv, u, sg, lnr, E, th;  // 1 + r, 1/(1 + r), u', sigma, log1p(r), expm1(x), theta
+};
+
+template <typename X>
+__device__ __forceinline__ void node_state_s(const X f[6], const Consts<X>& c, X m_s0h, NodeS<X>& m) {
+  // (ii) moments, eq. (M-d1q3q3), scaled.
+  const X tf = ad(f[1], f[2]), tg = ad(f[4], f[5]);
+  m.r = ad(tf, f[0]);
+  m.j = sb(f[1], f[2]);
+  m.e = fm(f[0], c.m_two, tf);
+  m.z = ad(tg, f[3]);
+  m.ps = sb(f[4], f[5]);
+  m.ep = fm(f[3], c.m_two, tg);
+  // Equation of state, eq. (gaz-parfait).
+  m.rho1 = ad(c.one, m.r);
+  m.inv = m_rcp(m.rho1);
+  m.u = ml(m.j, m.inv);
+  m.sg = ml(fm(m.r, m_s0h, m.z), m.inv);
+  m.lnr = m_log1p(m.r);
+  m.E = m_expm1(ml(c.gamma, ad(m.lnr, m.sg)));
+  m.th = ml(fm(c.kth, m.E, c.kth), m.inv);
+}
+
+template <typename X>
+__device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X thl, X thr, X s_e, X s_psi,
+                                               X s_eps, X q_src, X s0h, const Consts<X>& c, X fs[6]) {
+  // (iv) equilibria (eqs. energie-equilibre, psi-equilibre, eq-energie-entropie-d1q3q3).
+  const X sp = ad(s0h, m.sg);
+  const X e_eq = fm(m.r, c.m_two, ml(c.three, fm(m.j, m.u, ml(c.kp, m.E))));
+  const X ps_eq = ml(ml(m.rho1, sp), m.u);
+  const X ep_eq = fm(c.e_rs, m.sg, fm(e_eq, sp, ml(ad(m.rho1, m.rho1), fm(c.one_m_ig, m.lnr, m.sg))));
+  // (v) relaxation (eq. relaxation-d1q3q3).
+  const X es = fm(s_e, sb(e_eq, m.e), m.e);
+  const X pss = fm(s_psi, sb(ps_eq, m.ps), m.ps);
+  const X eps = fm(s_eps, sb(ep_eq, m.ep), m.ep);
+  // (vii) entropy production (eq. NS-rho-J-zeta), centred differences.
+  X zs = m.z;
+  if (c.source_on) {
+    const X du = sb(ur, ul), dth = sb(thr, thl);
+    const X ith = m_rcp(m.th);
+    const X A = fm(ml(dth, dth), ml(ith, c.inv_Pr), ml(du, du));
+    zs = fm(ml(ml(q_src, m.rho1), ith), A, m.z);
+  }
+  // (vi) back to populations.
+  {
+    const X h = ml(fm(m.r, c.two, es), c.sixth);
+    fs[0] = ml(sb(m.r, es), c.third);
+    fs[1] = fm(m.j, c.half, h);
+    fs[2] = fm(m.j, c.m_half, h);
+  }
+  {
+    const X h = ml(fm(zs, c.two, eps), c.sixth);
+    fs[3] = ml(sb(zs, eps), c.third);
+    fs[4] = fm(pss, c.half, h);
+    fs[5] = fm(pss, c.m_half, h);
   }
 }
 

@@ -33,7 +33,8 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   const int halo = 2 * K;
   const int bout = NT * V - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0 = R(d.s0);
+  const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0h = R(d.s0h);
+  const R m_s0h = -s0h;
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   R f[V][6];
@@ -55,14 +56,14 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   }
 
   for (int k = 0; k < K; ++k) {
-    Node<R> m[V];
+    NodeS<R> m[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) node_state(f[v], c, s0, m[v]);
-    // u, T of the neighbours of the first and last node of this thread.
-    R uL = __shfl_up_sync(0xffffffffu, m[V - 1].u, 1), TL = __shfl_up_sync(0xffffffffu, m[V - 1].T, 1);
-    R uR = __shfl_down_sync(0xffffffffu, m[0].u, 1), TR = __shfl_down_sync(0xffffffffu, m[0].T, 1);
-    if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].T; }
-    if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].T; }
+    for (int v = 0; v < V; ++v) node_state_s(f[v], c, m_s0h, m[v]);
+    // u' and theta of the neighbours of the first and last node of this thread.
+    R uL = __shfl_up_sync(0xffffffffu, m[V - 1].u, 1), TL = __shfl_up_sync(0xffffffffu, m[V - 1].th, 1);
+    R uR = __shfl_down_sync(0xffffffffu, m[0].u, 1), TR = __shfl_down_sync(0xffffffffu, m[0].th, 1);
+    if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].th; }
+    if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].th; }
     __syncthreads();
     if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
     if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
@@ -71,11 +72,11 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     R fs[V][6];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      R ul = v > 0 ? m[v - 1].u : uL, Tl = v > 0 ? m[v - 1].T : TL;
-      R ur = v < V - 1 ? m[v + 1].u : uR, Tr = v < V - 1 ? m[v + 1].T : TR;
-      if (lw[v]) { ul = -m[v].u; Tl = m[v].T; }
-      if (rw[v]) { ur = -m[v].u; Tr = m[v].T; }
-      node_collide(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0, c, fs[v]);
+      R ul = v > 0 ? m[v - 1].u : uL, Tl = v > 0 ? m[v - 1].th : TL;
+      R ur = v < V - 1 ? m[v + 1].u : uR, Tr = v < V - 1 ? m[v + 1].th : TR;
+      if (lw[v]) { ul = -m[v].u; Tl = m[v].th; }
+      if (rw[v]) { ur = -m[v].u; Tr = m[v].th; }
+      node_collide_s(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[v]);
     }
     // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
     R fpL = __shfl_up_sync(0xffffffffu, fs[V - 1][1], 1), gpL = __shfl_up_sync(0xffffffffu, fs[V - 1][4], 1);
@@ -122,7 +123,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   const long long off = d.offset, N = d.n;
   const float2 s_e = make_float2((float)d.s_e, (float)d.s_e), s_psi = make_float2((float)d.s_psi, (float)d.s_psi);
   const float2 s_eps = make_float2((float)d.s_eps, (float)d.s_eps), q_src = make_float2((float)d.q_src, (float)d.q_src);
-  const float2 s0 = make_float2((float)d.s0, (float)d.s0);
+  const float2 s0h = make_float2((float)d.s0h, (float)d.s0h), m_s0h = make_float2(-(float)d.s0h, -(float)d.s0h);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   float2 f[NL][6];
@@ -147,13 +148,13 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   }
 
   for (int k = 0; k < K; ++k) {
-    Node<float2> m[NL];
+    NodeS<float2> m[NL];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) node_state(f[l], c, s0, m[l]);
-    float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].T.y, 1);
-    float uR = __shfl_down_sync(0xffffffffu, m[0].u.x, 1), TR = __shfl_down_sync(0xffffffffu, m[0].T.x, 1);
-    if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].T.y; }
-    if (lane == 0) { e_ut[warp][2] = m[0].u.x; e_ut[warp][3] = m[0].T.x; }
+    for (int l = 0; l < NL; ++l) node_state_s(f[l], c, m_s0h, m[l]);
+    float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].th.y, 1);
+    float uR = __shfl_down_sync(0xffffffffu, m[0].u.x, 1), TR = __shfl_down_sync(0xffffffffu, m[0].th.x, 1);
+    if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].th.y; }
+    if (lane == 0) { e_ut[warp][2] = m[0].u.x; e_ut[warp][3] = m[0].th.x; }
     __syncthreads();
     if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
     if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
@@ -162,14 +163,14 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       float2 ul = make_float2(l > 0 ? m[l - 1].u.y : uL, m[l].u.x);
-      float2 Tl = make_float2(l > 0 ? m[l - 1].T.y : TL, m[l].T.x);
+      float2 Tl = make_float2(l > 0 ? m[l - 1].th.y : TL, m[l].th.x);
       float2 ur = make_float2(m[l].u.y, l < NL - 1 ? m[l + 1].u.x : uR);
-      float2 Tr = make_float2(m[l].T.y, l < NL - 1 ? m[l + 1].T.x : TR);
-      if (lw[2 * l]) { ul.x = -m[l].u.x; Tl.x = m[l].T.x; }
-      if (lw[2 * l + 1]) { ul.y = -m[l].u.y; Tl.y = m[l].T.y; }
-      if (rw[2 * l]) { ur.x = -m[l].u.x; Tr.x = m[l].T.x; }
-      if (rw[2 * l + 1]) { ur.y = -m[l].u.y; Tr.y = m[l].T.y; }
-      node_collide(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0, c, fs[l]);
+      float2 Tr = make_float2(m[l].th.y, l < NL - 1 ? m[l + 1].th.x : TR);
+      if (lw[2 * l]) { ul.x = -m[l].u.x; Tl.x = m[l].th.x; }
+      if (lw[2 * l + 1]) { ul.y = -m[l].u.y; Tl.y = m[l].th.y; }
+      if (rw[2 * l]) { ur.x = -m[l].u.x; Tr.x = m[l].th.x; }
+      if (rw[2 * l + 1]) { ur.y = -m[l].u.y; Tr.y = m[l].th.y; }
+      node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l]);
     }
     float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
     float fmR = __shfl_down_sync(0xffffffffu, fs[0][2].x, 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5].x, 1);

@@ -26,8 +26,9 @@ def test_paired_series_accuracy(fn_pair, fn_cuda, ref, lim):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     rng = np.random.default_rng(3)
-    x = np.concatenate([np.linspace(-lim, lim, 200001), rng.uniform(-0.9, 2.0, 100000),
-                        [-lim, lim, 0.0, 1e-30, -1e-20, 1e-7]]).astype(np.float32)
+    wide = rng.uniform(-0.95, 3.0, 200000) if fn_pair == 0 else rng.uniform(-6.0, 6.0, 200000)
+    x = np.concatenate([np.linspace(-lim, lim, 200001), wide,
+                        [-lim, lim, 0.0, 1e-30, -1e-20, 1e-7, 0.30001, -0.30001, 0.35001, -0.35001]]).astype(np.float32)
     x32 = x.astype(np.float64)
     exact = ref(x32)
     pair, cuda = _eval(x, fn_pair), _eval(x, fn_cuda)
