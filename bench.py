@@ -174,6 +174,17 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, dist, device: str = "cuda") -> float:
+    """The largest value over all ranks (the whole-job time of replicas started together)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_device(lat, torch, steps: int, warmup: int, dist, world: int):
     """Device-resident timing: K lattice steps between CUDA events on the library's stream."""
     st = lat.stream
@@ -186,11 +197,8 @@ def time_device(lat, torch, steps: int, warmup: int, dist, world: int):
     lat.step(steps)
     e1.record(st)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     return ms
 
@@ -335,11 +343,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     lat.step(K)
     lat.moments(out=outs + [None, None, None])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     lat.close()
     e2e = {"value": world * N_NODES * K / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 3 * 8 * N_NODES / K, "d2h_bytes_per_step": 3 * 8 * N_NODES / K}

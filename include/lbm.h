@@ -66,12 +66,18 @@ typedef struct {
 
 /* Physical constants shared by all lattices of a context. A NULL lbm_phys selects the section 9
  * values: gamma = 1.4, Pr = 1, c_p = 1, rho0 = 1, s0 = 0, p0 = rho0 c0^2 / gamma with
- * c0 = lambda / 2, source on. p0 <= 0 selects that p0 as well. rho0 is both the scale of M
- * (eq. M-d1q3q3) and the reference density of eq. (gaz-parfait); s0 its reference entropy. */
+ * c0 = lambda / 2, source on, nonlinear equilibria. p0 <= 0 selects that p0 as well. rho0 is both
+ * the scale of M (eq. M-d1q3q3) and the reference density of eq. (gaz-parfait); s0 its reference
+ * entropy.
+ * equilibria = 0: the nonlinear equilibria of section 8. equilibria = 1: the linear equilibria of
+ *   eq. (equilibres-NS-linearise) (section 7) around the state (rho0, u0_lin, s0_lin) with
+ *   c0^2 = gamma p0 / rho0, as printed; their units hold only for lambda = c_p = 1, which is
+ *   required, and the linearised system has no entropy production, so source_on must be 0. */
 typedef struct {
   double gamma, Pr, cp, rho0, p0, s0;
-  int32_t source_on; /* 1: entropy-production source of eq. (NS-rho-J-zeta); 0: off */
-  int32_t reserved;  /* must be 0 */
+  int32_t source_on;  /* 1: entropy-production source of eq. (NS-rho-J-zeta); 0: off */
+  int32_t equilibria; /* 0 nonlinear (section 8), 1 linear (section 7) */
+  double u0_lin, s0_lin;
 } lbm_phys;
 
 /* Device allocator used for all device memory of contexts created afterwards.

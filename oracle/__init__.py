@@ -49,19 +49,33 @@ class Phys(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("cp", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("p0", ctypes.c_double), ("s0", ctypes.c_double),
                 ("lam", ctypes.c_double), ("dx", ctypes.c_double),
-                ("source_on", ctypes.c_int32), ("bc", ctypes.c_int32)]
+                ("source_on", ctypes.c_int32), ("bc", ctypes.c_int32),
+                ("eq_mode", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("u0_lin", ctypes.c_double), ("s0_lin", ctypes.c_double)]
 
 
 def default_phys(**kw) -> Phys:
-    """Section 9 parameters; keyword overrides: gamma, Pr, cp, rho0, p0, s0, lam, dx, source_on, bc."""
+    """Section 9 parameters; keyword overrides: gamma, Pr, cp, rho0, p0, s0, lam, dx, source_on, bc,
+    eq_mode (1: the linear equilibria of section 7 around u0_lin, s0_lin; the source is then off by
+    default since the linearised system has no production term)."""
     lam = kw.get("lam", 1.0)
     gamma = kw.get("gamma", 1.4)
     rho0 = kw.get("rho0", 1.0)
     c0 = lam / 2.0
     ph = Phys(gamma=gamma, Pr=kw.get("Pr", 1.0), cp=kw.get("cp", 1.0), rho0=rho0,
               p0=kw.get("p0", rho0 * c0 * c0 / gamma), s0=kw.get("s0", 0.0), lam=lam,
-              dx=kw.get("dx", 1.0), source_on=int(kw.get("source_on", 1)), bc=int(kw.get("bc", 0)))
+              dx=kw.get("dx", 1.0), source_on=int(kw.get("source_on", 0 if kw.get("eq_mode", 0) else 1)),
+              bc=int(kw.get("bc", 0)), eq_mode=int(kw.get("eq_mode", 0)), pad=0,
+              u0_lin=kw.get("u0_lin", 0.0), s0_lin=kw.get("s0_lin", 0.0))
     return ph
+
+
+def linear_rates(s_e: float, gamma: float = 1.4, Pr: float = 1.0) -> np.ndarray:
+    """Rates of the section 7 linear scheme: s_psi from eq. (lien-sigma-sigma), sigma_eps = 1.5
+    (so s_eps = 1/(1.5 + 1/2) = 0.5), as section 7 states."""
+    r = coupled_rates(s_e, gamma, Pr)
+    r[2] = 1.0 / (1.5 + 0.5)
+    return r
 
 
 def _load():

@@ -75,6 +75,11 @@ struct Phys {
   double gamma, Pr, cp, rho0, p0, s0, lambda, dx;
   int32_t source_on;
   int32_t bc;  // 0 periodic, 1 halfway bounce-back at both ends
+  // Equilibria: 0 the nonlinear ones of section 8; 1 the linear ones of eq. (equilibres-NS-linearise)
+  // (section 7) around the state of velocity u0_lin and specific entropy s0_lin.
+  int32_t eq_mode;
+  int32_t pad;
+  double u0_lin, s0_lin;
 };
 
 template <class R>
@@ -152,6 +157,19 @@ inline void equilibria(const Phys& ph, const R& rho, const R& u, const R& zeta, 
                        const R& p, const R& T, R& e_eq, R& psi_eq, R& eps_eq) {
   using std::log;
   const double l2 = ph.lambda * ph.lambda;
+  if (ph.eq_mode == 1) {
+    // Eq. (equilibres-NS-linearise), as printed (lattice units lambda = c_p = 1), linear in
+    // (rho, J, zeta) around (rho0, u0, s0) with c0^2 = gamma p0 / rho0.
+    const double u0 = ph.u0_lin, s0 = ph.s0_lin, cp = ph.cp, g = ph.gamma;
+    const double c02 = g * ph.p0 / ph.rho0;
+    const R J = rho * u;
+    e_eq = (3.0 * (1.0 - s0 / cp) * c02 - 3.0 * u0 * u0 - 2.0 * l2) * rho + 6.0 * u0 * J + 3.0 * (u0 * u0 / cp) * zeta;
+    psi_eq = -u0 * s0 * rho + s0 * J + u0 * zeta;
+    eps_eq = (-3.0 * (s0 * s0 * c02) - 6.0 * s0 * u0 * u0 + 3.0 * s0 * c02 + 2.0 - 2.0 * s0 - 2.0 / g) * rho +
+             6.0 * u0 * s0 * J + 3.0 * (cp * u0 * u0 + s0 * c02) * zeta;
+    (void)s; (void)p; (void)T;
+    return;
+  }
   e_eq = 3.0 * (rho * u * u + p) - 2.0 * l2 * rho;                        // eq. energie-equilibre
   psi_eq = zeta * u;                                                      // eq. psi-equilibre
   eps_eq = (2.0 * rho * ph.cp * l2 / ph.gamma) * log(T / T_ref(ph)) + e_eq * s;  // eq. eq-energie-entropie
@@ -276,6 +294,9 @@ bool valid(const Phys* ph, int64_t N) {
   if (!(ph->lambda > 0) || !(ph->dx > 0) || !(ph->gamma > 1) || !(ph->cp > 0) || !(ph->rho0 > 0) ||
       !(ph->p0 > 0) || !(ph->Pr > 0))
     return false;
+  // The printed linear equilibria are consistent in units only for lambda = c_p = 1.
+  if (ph->eq_mode == 1 && (ph->lambda != 1.0 || ph->cp != 1.0)) return false;
+  if (ph->eq_mode != 0 && ph->eq_mode != 1) return false;
   return ph->bc == 0 || ph->bc == 1;
 }
 

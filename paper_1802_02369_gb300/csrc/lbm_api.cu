@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.cuh"
 
@@ -30,6 +32,15 @@ void* g_user = nullptr;
 struct PhysD {
   double gamma, Pr, cp, rho0, p0, s0, lam;
   int source_on;
+  int eq_mode;            // 0 nonlinear (section 8), 1 linear (section 7)
+  double u0_lin, s0_lin;  // state of the linearisation (eq_mode 1)
+  double c02() const { return gamma * p0 / rho0; }
+  // Coefficients of the linear equilibria of eq. (equilibres-NS-linearise) on rho (lambda = c_p = 1).
+  double lin_a1() const { return 3.0 * (1.0 - s0_lin / cp) * c02() - 3.0 * u0_lin * u0_lin - 2.0 * lam * lam; }
+  double lin_b1() const {
+    return -3.0 * (s0_lin * s0_lin * c02()) - 6.0 * s0_lin * u0_lin * u0_lin + 3.0 * s0_lin * c02() + 2.0 -
+           2.0 * s0_lin - 2.0 / gamma;
+  }
   double r() const { return cp * (1.0 - 1.0 / gamma); }
   double e_r() const { return 3.0 * p0 - 2.0 * lam * lam * rho0; }
   double wf0() const { return 1.0 - p0 / (rho0 * lam * lam); }  // rest populations of f
@@ -83,6 +94,19 @@ Consts<X> make_consts(const PhysD& p) {
   c.e_rs = lift<X>(3.0 * kp - 2.0);
   c.one_m_ig = lift<X>(1.0 - 1.0 / p.gamma);
   c.inv_Pr = lift<X>(1.0 / p.Pr);
+  {
+    const double u0 = p.u0_lin, s0 = p.s0_lin;
+    c.leR = lift<X>(p.lin_a1());
+    c.leJ = lift<X>(6.0 * u0);
+    c.leZ = lift<X>(3.0 * u0 * u0);
+    c.lpR = lift<X>(-u0 * s0);
+    c.lpJ = lift<X>(s0);
+    c.lpZ = lift<X>(u0);
+    c.lqR = lift<X>(p.lin_b1());
+    c.lqJ = lift<X>(6.0 * u0 * s0);
+    c.lqZ = lift<X>(3.0 * (u0 * u0 + s0 * p.c02()));
+  }
+  c.eq_mode = p.eq_mode;
   c.source_on = p.source_on;
   return c;
 }
@@ -135,6 +159,8 @@ __device__ __forceinline__ int lattice_of_node(const LatDev* lat, int B, long lo
 
 struct InitArgs {
   double rho0, p0, gamma, cp, lam, e_r, cp_log, wf0, wf1;
+  int eq_mode;
+  double u0_lin, s0_lin, a1, b1, c02;
 };
 
 // Equilibrium populations from (rho, u, p) (from_p = 1) or (rho, u, s) (from_p = 0), computed in
@@ -154,9 +180,18 @@ __global__ void init_kernel(const double* __restrict__ rho_in, const double* __r
   const double rt = rho - a.rho0, J = rho * u;
   const double zeta = rho * s, zt = zeta - d.zeta_r;
   const double l2 = a.lam * a.lam;
-  const double e_t = 3.0 * (J * u + pt) - 2.0 * l2 * rt;
-  const double psi = zeta * u;
-  const double eps_t = 2.0 * l2 * rho * (ds + a.cp_log * lnr) + e_t * s + a.e_r * ds;
+  double e_t, psi, eps_t;
+  if (a.eq_mode == 1) {
+    // Eq. (equilibres-NS-linearise), lambda = c_p = 1, shifted by the rest moments.
+    const double u0 = a.u0_lin, s0 = a.s0_lin;
+    e_t = a.a1 * rho + 6.0 * u0 * J + 3.0 * (u0 * u0 / a.cp) * zeta - a.e_r;
+    psi = -u0 * s0 * rho + s0 * J + u0 * zeta;
+    eps_t = a.b1 * rho + 6.0 * u0 * s0 * J + 3.0 * (a.cp * u0 * u0 + s0 * a.c02) * zeta - a.e_r * d.s0;
+  } else {
+    e_t = 3.0 * (J * u + pt) - 2.0 * l2 * rt;
+    psi = zeta * u;
+    eps_t = 2.0 * l2 * rho * (ds + a.cp_log * lnr) + e_t * s + a.e_r * ds;
+  }
   const double af = a.rho0, ag = a.rho0 * a.cp;
   double r = rt / af, j = J / (af * a.lam), q = e_t / (af * l2);
   st[0 * plane + i] = R((r - q) / 3.0);
@@ -375,6 +410,12 @@ struct lbm_ctx {
 
 namespace {
 
+// NVTX range for the duration of a C-ABI call (visible in Nsight timelines; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 int fail(lbm_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -401,6 +442,12 @@ InitArgs init_args(const lbm_ctx* c) {
   a.cp_log = (1.0 - 1.0 / c->ph.gamma) * c->ph.cp;
   a.wf0 = c->ph.wf0();
   a.wf1 = c->ph.wf1();
+  a.eq_mode = c->ph.eq_mode;
+  a.u0_lin = c->ph.u0_lin;
+  a.s0_lin = c->ph.s0_lin;
+  a.a1 = c->ph.lin_a1();
+  a.b1 = c->ph.lin_b1();
+  a.c02 = c->ph.c02();
   return a;
 }
 
@@ -465,11 +512,16 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   ph.rho0 = phys ? phys->rho0 : 1.0;
   ph.s0 = phys ? phys->s0 : 0.0;
   ph.source_on = phys ? (phys->source_on != 0) : 1;
+  ph.eq_mode = phys ? phys->equilibria : 0;
+  ph.u0_lin = phys ? phys->u0_lin : 0.0;
+  ph.s0_lin = phys ? phys->s0_lin : 0.0;
   const double c0 = lambda / 2.0;
   ph.p0 = (phys && phys->p0 > 0.0) ? phys->p0 : ph.rho0 * c0 * c0 / ph.gamma;
   if (!(ph.gamma > 1.0) || !(ph.Pr > 0.0) || !(ph.cp > 0.0) || !(ph.rho0 > 0.0) || !(ph.p0 > 0.0))
     return LBM_ERR_INVALID_ARG;
-  if (phys && phys->reserved != 0) return LBM_ERR_INVALID_ARG;
+  if (ph.eq_mode != 0 && ph.eq_mode != 1) return LBM_ERR_INVALID_ARG;
+  // The printed linear equilibria hold in lattice units lambda = c_p = 1, without the source.
+  if (ph.eq_mode == 1 && (lambda != 1.0 || ph.cp != 1.0 || ph.source_on)) return LBM_ERR_INVALID_ARG;
 
   lbm_ctx* c = new lbm_ctx();
   c->B = B;
@@ -513,6 +565,14 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
       d.wg1 = (2.0 * r0 + q0) / 6.0;
     }
     d.s0h = c->s0[b] / ph.cp;
+    {
+      // Constant terms of the linear equilibria in scaled shifted moments (lambda = c_p = 1):
+      // x_eq = x0 + xR r + xJ j + xZ z with rho/rho0 = 1 + r, J/rho0 = j, zeta/rho0 = z + s0/c_p.
+      const double u0 = ph.u0_lin, s0l = ph.s0_lin, sh = d.s0h, er = ph.e_r() / (ph.rho0 * lambda * lambda);
+      d.lin_e0 = ph.lin_a1() + 3.0 * u0 * u0 * sh - er;
+      d.lin_p0 = -u0 * s0l + u0 * sh;
+      d.lin_q0 = ph.lin_b1() + 3.0 * (u0 * u0 + s0l * ph.c02()) * sh - er * sh;
+    }
     d.bc = bc[b];
     d.pad = 0;
     tot += N[b];
@@ -713,6 +773,7 @@ int lbm_set_state_entropy(lbm_ctx* c, const double* rho, const double* u, const 
 }
 
 int lbm_step(lbm_ctx* c, int64_t nsteps) {
+  NvtxRange r("lbm_step");
   if (!c) return LBM_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "step: nsteps < 0");
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "step: no state set");
@@ -811,6 +872,7 @@ int lbm_set_populations(lbm_ctx* c, const double* fd) {
 }
 
 int lbm_diagnostics(lbm_ctx* c, double* sums, int32_t* flags) {
+  NvtxRange r("lbm_diagnostics");
   if (!c || !sums || !flags) return LBM_ERR_INVALID_ARG;
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "diagnostics: no state set");
   const InitArgs a = init_args(c);
@@ -857,6 +919,7 @@ int lbm_get_config(const lbm_ctx* c, int32_t* k, int32_t* nt, int32_t* v) {
 }
 
 int lbm_autotune(lbm_ctx* c, int32_t trials) {
+  NvtxRange r("lbm_autotune");
   if (!c || trials < 1) return LBM_ERR_INVALID_ARG;
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "autotune: no state set");
   cudaEvent_t e0, e1;
@@ -1081,13 +1144,16 @@ int adjoint_backward_impl(lbm_ctx* c, const double* target, const double* rho_b,
 extern "C" {
 
 int lbm_adjoint_forward(lbm_ctx* c, int64_t T) {
+  NvtxRange r("lbm_adjoint_forward");
   if (!c || T < 1) return LBM_ERR_INVALID_ARG;
+  if (c->ph.eq_mode != 0) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: only the nonlinear equilibria are differentiated");
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: no state set");
   return c->precision == LBM_F64 ? adjoint_forward_impl<double>(c, T) : adjoint_forward_impl<float>(c, T);
 }
 
 int lbm_adjoint_backward(lbm_ctx* c, const double* dL_drho_T, double* dL_drho0, double* dL_du0, double* dL_drates,
                          double* dL_dfd0) {
+  NvtxRange r("lbm_adjoint_backward");
   if (!c || !dL_drho_T) return LBM_ERR_INVALID_ARG;
   return c->precision == LBM_F64
              ? adjoint_backward_impl<double>(c, nullptr, dL_drho_T, nullptr, dL_drho0, dL_du0, dL_drates, dL_dfd0)

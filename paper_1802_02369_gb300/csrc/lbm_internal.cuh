@@ -19,6 +19,7 @@ struct LatDev {
   double eps_r;    //   eps_r = e_r s0 (e_r = 3 p0 - 2 lambda^2 rho0)
   double wg0, wg1; // rest g populations (g0, g+ = g-)
   double s0h;      // s0 / c_p
+  double lin_e0, lin_p0, lin_q0;  // constant terms of the linear equilibria in scaled moments
   int bc, pad;
 };
 
@@ -44,6 +45,9 @@ struct Consts {
   X e_rs;      // e_r / (rho0 lambda^2) = 3 kp - 2
   X one_m_ig;  // 1 - 1/gamma
   X inv_Pr;    // 1 / Pr
+  // Linear equilibria (section 7) in scaled moments: x_eq = x0 (per lattice) + xR r + xJ j + xZ z.
+  X leR, leJ, leZ, lpR, lpJ, lpZ, lqR, lqJ, lqZ;
+  int eq_mode;   // 0 nonlinear (section 8), 1 linear (section 7)
   int source_on;
 };
 
@@ -242,6 +246,10 @@ __device__ __forceinline__ void node_state_s(const X f[6], const Consts<X>& c, X
   m.ep = fm(f[3], c.m_two, tg);
   // Equation of state, eq. (gaz-parfait).
   m.rho1 = ad(c.one, m.r);
+  if (c.eq_mode == 1) {  // the linear equilibria need no equation of state (and there is no source)
+    m.inv = m.u = m.sg = m.lnr = m.E = m.th = X{};
+    return;
+  }
   m.inv = m_rcp(m.rho1);
   m.u = ml(m.j, m.inv);
   m.sg = ml(fm(m.r, m_s0h, m.z), m.inv);
@@ -252,12 +260,21 @@ __device__ __forceinline__ void node_state_s(const X f[6], const Consts<X>& c, X
 
 template <typename X>
 __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X thl, X thr, X s_e, X s_psi,
-                                               X s_eps, X q_src, X s0h, const Consts<X>& c, X fs[6]) {
-  // (iv) equilibria (eqs. energie-equilibre, psi-equilibre, eq-energie-entropie-d1q3q3).
-  const X sp = ad(s0h, m.sg);
-  const X e_eq = fm(m.r, c.m_two, ml(c.three, fm(m.j, m.u, ml(c.kp, m.E))));
-  const X ps_eq = ml(ml(m.rho1, sp), m.u);
-  const X ep_eq = fm(c.e_rs, m.sg, fm(e_eq, sp, ml(ad(m.rho1, m.rho1), fm(c.one_m_ig, m.lnr, m.sg))));
+                                               X s_eps, X q_src, X s0h, const Consts<X>& c, X fs[6],
+                                               X lin_e0 = X{}, X lin_p0 = X{}, X lin_q0 = X{}) {
+  // (iv) equilibria (eqs. energie-equilibre, psi-equilibre, eq-energie-entropie-d1q3q3), or the
+  // linear ones of eq. (equilibres-NS-linearise).
+  X e_eq, ps_eq, ep_eq;
+  if (c.eq_mode == 1) {
+    e_eq = fm(c.leZ, m.z, fm(c.leJ, m.j, fm(c.leR, m.r, lin_e0)));
+    ps_eq = fm(c.lpZ, m.z, fm(c.lpJ, m.j, fm(c.lpR, m.r, lin_p0)));
+    ep_eq = fm(c.lqZ, m.z, fm(c.lqJ, m.j, fm(c.lqR, m.r, lin_q0)));
+  } else {
+    const X sp = ad(s0h, m.sg);
+    e_eq = fm(m.r, c.m_two, ml(c.three, fm(m.j, m.u, ml(c.kp, m.E))));
+    ps_eq = ml(ml(m.rho1, sp), m.u);
+    ep_eq = fm(c.e_rs, m.sg, fm(e_eq, sp, ml(ad(m.rho1, m.rho1), fm(c.one_m_ig, m.lnr, m.sg))));
+  }
   // (v) relaxation (eq. relaxation-d1q3q3).
   const X es = fm(s_e, sb(e_eq, m.e), m.e);
   const X pss = fm(s_psi, sb(ps_eq, m.ps), m.ps);

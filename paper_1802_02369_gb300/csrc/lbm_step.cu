@@ -35,6 +35,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   const long long off = d.offset, N = d.n;
   const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0h = R(d.s0h);
   const R m_s0h = -s0h;
+  const R le0 = R(d.lin_e0), lp0 = R(d.lin_p0), lq0 = R(d.lin_q0);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   R f[V][6];
@@ -76,7 +77,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
       R ur = v < V - 1 ? m[v + 1].u : uR, Tr = v < V - 1 ? m[v + 1].th : TR;
       if (lw[v]) { ul = -m[v].u; Tl = m[v].th; }
       if (rw[v]) { ur = -m[v].u; Tr = m[v].th; }
-      node_collide_s(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[v]);
+      node_collide_s(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[v], le0, lp0, lq0);
     }
     // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
     R fpL = __shfl_up_sync(0xffffffffu, fs[V - 1][1], 1), gpL = __shfl_up_sync(0xffffffffu, fs[V - 1][4], 1);
@@ -124,6 +125,8 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   const float2 s_e = make_float2((float)d.s_e, (float)d.s_e), s_psi = make_float2((float)d.s_psi, (float)d.s_psi);
   const float2 s_eps = make_float2((float)d.s_eps, (float)d.s_eps), q_src = make_float2((float)d.q_src, (float)d.q_src);
   const float2 s0h = make_float2((float)d.s0h, (float)d.s0h), m_s0h = make_float2(-(float)d.s0h, -(float)d.s0h);
+  const float2 le0 = make_float2((float)d.lin_e0, (float)d.lin_e0), lp0 = make_float2((float)d.lin_p0, (float)d.lin_p0);
+  const float2 lq0 = make_float2((float)d.lin_q0, (float)d.lin_q0);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   float2 f[NL][6];
@@ -170,7 +173,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
       if (lw[2 * l + 1]) { ul.y = -m[l].u.y; Tl.y = m[l].th.y; }
       if (rw[2 * l]) { ur.x = -m[l].u.x; Tr.x = m[l].th.x; }
       if (rw[2 * l + 1]) { ur.y = -m[l].u.y; Tr.y = m[l].th.y; }
-      node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l]);
+      node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l], le0, lp0, lq0);
     }
     float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
     float fmR = __shfl_down_sync(0xffffffffu, fs[0][2].x, 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5].x, 1);

@@ -53,7 +53,8 @@ class lbm_rates(ctypes.Structure):
 class lbm_phys(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("cp", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("p0", ctypes.c_double), ("s0", ctypes.c_double),
-                ("source_on", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("source_on", ctypes.c_int32), ("equilibria", ctypes.c_int32),
+                ("u0_lin", ctypes.c_double), ("s0_lin", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -200,7 +201,8 @@ class Lattice:
     lengths: int or sequence of ints (>= 3). s_e: the free rate (scalar or per lattice).
     s_psi / s_eps: <= 0 selects the paper's coupling / 1.5. bc: 0 periodic, 1 bounce-back
     (scalar or per lattice). precision: "f64" or "f32" (FP32 shifted populations).
-    s0: per-lattice reference entropy (None: phys["s0"]). phys: dict of lbm_phys fields.
+    s0: per-lattice reference entropy (None: phys["s0"]). phys: dict of lbm_phys fields
+    (e.g. dict(equilibria=1, u0_lin=0.15, s0_lin=0.2, source_on=0) for the section 7 linear scheme).
     """
 
     def __init__(self, lengths, lam: float = 1.0, s_e=1.5, s_psi=0.0, s_eps=0.0, bc=0,
@@ -217,7 +219,8 @@ class Lattice:
         rates = (lbm_rates * B)(*[lbm_rates(float(a), float(b), float(c)) for a, b, c in zip(s_e, s_psi, s_eps)])
         ph = None
         if phys is not None:
-            base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, source_on=1, reserved=0)
+            base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, source_on=1, equilibria=0,
+                        u0_lin=0.0, s0_lin=0.0)
             base.update(phys)
             ph = lbm_phys(**base)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

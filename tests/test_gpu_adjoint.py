@@ -147,3 +147,45 @@ def test_autograd_function_matches_adjoint(lbm):
     np.testing.assert_allclose(u0.grad.cpu().numpy(), du, rtol=1e-10, atol=1e-14)
     np.testing.assert_allclose(se_t.grad.cpu().numpy(), drates[:, 0], rtol=1e-10)
     np.testing.assert_allclose(sp_t.grad.cpu().numpy(), drates[:, 1], rtol=1e-10)
+
+
+def test_adjoint_bump_batch_probe_directions(lbm):
+    """The differentiation workload's shape (Gaussian density bumps, seed 2369, target from seed
+    2370, lattices of 65536 nodes), reduced to 4 lattices and T = 400 for test time: the FP64
+    adjoint gradient against central differences (h = 1e-6) of the GPU forward on 8 random probe
+    directions in (rho0, u0), within 1e-6 relative."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    B, N, T = 4, 65536, 400
+    p_ref = W.reference_pressure()
+    rho, u, p = W.gaussian_bumps(B, N, 2369, p_ref)
+    rt, ut, pt = W.gaussian_bumps(B, N, 2370, p_ref)
+    s_e = 1.5
+    ref = lbm.Lattice(np.full(B, N), s_e=s_e)
+    ref.set_state(rt.ravel(), ut.ravel(), pt.ravel())
+    ref.step(T)
+    target = ref.moments(device=False)[0]
+    ref.close()
+    lat = lbm.Lattice(np.full(B, N), s_e=s_e)
+    lat.set_state(rho.ravel(), u.ravel(), p.ravel())
+    s0 = np.asarray(lat.moments(device=False)[2]) / rho.ravel()   # initial specific entropy
+    loss, drho, du, drates = lat.adjoint(T, target)
+    lat.close()
+
+    def L(r, v):
+        x = lbm.Lattice(np.full(B, N), s_e=s_e)
+        x.set_state_entropy(r, v, s0)
+        x.step(T)
+        out = float(np.sum((np.asarray(x.moments(device=False)[0]) - target) ** 2))
+        x.close()
+        return out
+
+    rng = np.random.default_rng(2369)
+    h = 1e-6
+    r0, u0 = rho.ravel(), u.ravel()
+    for _ in range(8):
+        vr = rng.standard_normal(r0.size)
+        vu = rng.standard_normal(r0.size)
+        fdiff = (L(r0 + h * vr, u0 + h * vu) - L(r0 - h * vr, u0 - h * vu)) / (2 * h)
+        grad = np.dot(drho, vr) + np.dot(du, vu)
+        assert abs(grad - fdiff) <= 1e-6 * abs(grad), (grad, fdiff)

@@ -392,3 +392,40 @@ def test_precision_sweep_amplitude_02(O, lbm):
         _, flags, rc = lat.diagnostics()
         assert rc == lbm.LBM_ERR_UNSTABLE and np.all(flags != 0), (precision, flags)
         lat.close()
+
+
+@pytest.mark.parametrize("u0,s0", [(0.0, 0.0), (0.15, 0.2)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_linear_variant_section7(O, lbm, u0, s0, precision, tol):
+    """The section 7 scheme (linear equilibria of eq. (equilibres-NS-linearise) around (rho0, u0,
+    s0), sigma_eps = 1.5, no source) on small acoustic waves (figure 1 amplitude, delta = 1e-3) in
+    two lattices (periodic, and bounce-back at rest): GPU against the oracle's linear mode."""
+    lengths = np.array([4099, 777])
+    bcs = np.array([0, 1])
+    s_e = 1.9
+    rates = O.linear_rates(s_e)
+    phys = dict(equilibria=1, u0_lin=u0, s0_lin=s0, source_on=0)
+    fields, refs = [], []
+    for n, bc in zip(lengths, bcs):
+        x = 2 * np.pi * np.arange(n) / n
+        rho = 1.0 + 1e-3 * np.sin(x)
+        u = (u0 if bc == 0 else 0.0) + 0.5e-3 * np.sin(x) * (np.sin(np.pi * (np.arange(n) + 0.5) / n) if bc else 1)
+        s = np.full(n, s0)
+        ph = O.default_phys(eq_mode=1, u0_lin=u0, s0_lin=s0, bc=int(bc))
+        refs.append(O.moments(ph, O.run(ph, rates, O.init(ph, rho, u, s=s), 500, NTHREADS)))
+        fields.append((rho, u, s))
+    lat = lbm.Lattice(lengths, s_e=s_e, s_eps=rates[2], bc=bcs, precision=precision, phys=phys)
+    lat.set_state_entropy(*[np.concatenate([f[k] for f in fields]) for k in range(3)])
+    lat.step(500)
+    g = np.stack(lat.moments(device=False), axis=1)
+    lat.close()
+    off = np.r_[0, np.cumsum(lengths)]
+    for b in range(2):
+        assert rel_err(list(g[off[b]:off[b + 1]].T), refs[b], scales()).max() <= tol, b
+
+
+def test_linear_variant_rejects_inconsistent_units(lbm):
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(64, lam=2.0, phys=dict(equilibria=1, source_on=0))
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(64, phys=dict(equilibria=1, source_on=1))
