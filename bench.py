@@ -245,6 +245,31 @@ def run_batched(args, lbm, torch, hbm_peak, world):
                          "effective_frac": glups / world * BYTES_PER_NODE["f32"] / hbm_peak}}
 
 
+def run_linear(args, lbm, torch):
+    """The section 7 linear scheme (linear equilibria around u0 = 0.15, s0 = 0.2, sigma_eps = 1.5,
+    no source) on a small acoustic wave, N = 2^26, autotuned, FP32 and FP64."""
+    N = N_NODES
+    x = 2 * np.pi * np.arange(N) / N
+    rho = torch.from_numpy(1.0 + 1e-3 * np.sin(x)).cuda()
+    u = torch.from_numpy(0.15 + 0.5e-3 * np.sin(x)).cuda()
+    s = torch.full((N,), 0.2, dtype=torch.float64, device="cuda")
+    out = {}
+    for prec, steps in (("f32", 1000), ("f64", 200)):
+        lat = lbm.Lattice(N, s_e=1.9, s_eps=0.5, precision=prec,
+                          phys=dict(equilibria=1, u0_lin=0.15, s0_lin=0.2, source_on=0))
+        lat.set_state_entropy(rho, u, s)
+        k, nt, v = lat.autotune(1)
+        lat.set_state_entropy(rho, u, s)
+        steps = (steps // k) * k
+        ms = time_device(lat, torch, steps, 3 * k, None, 1)
+        lat.close()
+        out[prec] = {"value": N * steps / (ms * 1e-3) / 1e9, "unit": UNIT, "steps": steps, "steps_per_launch": k,
+                     "block_threads": nt, "nodes_per_thread": v}
+    del rho, u, s
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_adjoint(args, lbm, torch):
     """Gradient of sum (rho_T - rho*)^2 for 256 lattices of 65536 nodes (Gaussian density bumps,
     seed 2369; target from seed 2370), sqrt(T) checkpointing. Reported: node-steps of the
@@ -349,6 +374,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
            "h2d_bytes_per_step": 3 * 8 * N_NODES / K, "d2h_bytes_per_step": 3 * 8 * N_NODES / K}
 
     batched = None if args.no_batched else run_batched(args, lbm, torch, hbm_peak, world)
+    linear = None if args.no_linear else run_linear(args, lbm, torch)
     adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch)
 
     if rank != 0:
@@ -385,7 +411,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                      "steps_per_launch": f64["k"], "block_threads": f64["block_threads"],
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof(f64, "f64")},
-            "batched_fp32": batched, "adjoint": adjoint,
+            "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
     print(json.dumps(line), flush=True)
@@ -405,6 +431,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-linear", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps-f32", type=int, default=4000)
     ap.add_argument("--adjoint-steps-f64", type=int, default=1000)

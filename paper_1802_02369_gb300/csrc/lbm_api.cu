@@ -369,6 +369,8 @@ struct lbm_ctx {
   std::vector<LatDev> host_tabs;    //   host_tabs[k * B .. k * B + B - 1]
   LatDev* d_lat = nullptr;          // 4 * B records on the device, same layout
   long long ntiles_k[4] = {0, 0, 0, 0};
+  int* d_tile_lat = nullptr;        // per depth k: lattice of each tile, at d_tile_lat + k * max_tiles
+  long long max_tiles = 0;
   void* state[2] = {nullptr, nullptr};
   int cur = 0;
   bool has_state = false;
@@ -480,12 +482,21 @@ void rebuild_tables(lbm_ctx* c) {
 int upload_lat(lbm_ctx* c) {
   LBM_CK(c, cudaMemcpyAsync(c->d_lat, c->host_tabs.data(), sizeof(LatDev) * 4 * c->B, cudaMemcpyHostToDevice,
                             c->stream));
+  if (c->d_tile_lat)
+    for (int ki = 0; ki < 4; ++ki) {
+      if (c->ntiles_k[ki] > c->max_tiles) return fail(c, LBM_ERR_INVALID_ARG, "tile table overflow");
+      LBM_CK(c, lbm::launch_tile_map(c->d_lat + ki * (size_t)c->B, c->B, c->ntiles_k[ki],
+                                     c->d_tile_lat + ki * c->max_tiles, c->stream));
+    }
   LBM_CK(c, cudaStreamSynchronize(c->stream));  // host_tabs may change again before the copy runs
   return LBM_OK;
 }
 
-// Device table for depth K.
+inline const int* tile_map_for(const lbm_ctx* c, int K);
+
+// Device tables for depth K.
 inline const LatDev* lat_for(const lbm_ctx* c, int K) { return c->d_lat + depth_index(K) * (size_t)c->B; }
+inline const int* tile_map_for(const lbm_ctx* c, int K) { return c->d_tile_lat + depth_index(K) * c->max_tiles; }
 
 int ensure_stage(lbm_ctx* c, size_t bytes) {
   if (c->stage_bytes >= bytes) return LBM_OK;
@@ -594,12 +605,14 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   {
     long long max_tiles = 0;  // narrowest tiles: 128 threads x 1 node, depth 8
     for (int b = 0; b < B; ++b) max_tiles += (c->N[b] + (128 - 32) - 1) / (128 - 32);
+    c->max_tiles = max_tiles;
     c->d_done = (int*)dev_alloc(sizeof(int) * max_tiles, c->stream);
+    c->d_tile_lat = (int*)dev_alloc(sizeof(int) * 4 * max_tiles, c->stream);
   }
   c->d_counter = (unsigned long long*)dev_alloc(sizeof(unsigned long long), c->stream);
   c->d_status = (int*)dev_alloc(sizeof(int), c->stream);
   if (!c->d_lat || !c->state[0] || !c->state[1] || !c->d_sums || !c->d_flags || !c->d_part || !c->d_pflag ||
-      !c->d_done || !c->d_counter || !c->d_status) {
+      !c->d_done || !c->d_counter || !c->d_status || !c->d_tile_lat) {
     lbm_destroy(c);
     return LBM_ERR_OOM;
   }
@@ -614,12 +627,13 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
 template <typename R>
 cudaError_t enqueue_persistent(lbm_ctx* c, long long nblocks, cudaStream_t st, const lbm::ConstSet<R>& k) {
   const int ki = depth_index(c->K);
-  cudaError_t e = cudaMemsetAsync(c->d_done, 0, sizeof(int) * c->ntiles_k[ki], st);
+  cudaError_t e = cudaMemsetAsync(c->d_done, 0, sizeof(int) * ((c->ntiles_k[ki] + lbm::kUnitTiles - 1) / lbm::kUnitTiles), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   lbm::PersistentCtl ctl{c->d_counter, c->d_done, c->d_status, c->spin_limit, c->withhold};
-  return lbm::launch_persistent<R>((R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot, lat_for(c, c->K), c->B,
-                                   c->ntiles_k[ki], c->K, c->NT, c->V, nblocks, ctl, k, st);
+  return lbm::launch_persistent<R>((R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot, lat_for(c, c->K),
+                                   tile_map_for(c, c->K), c->B, c->ntiles_k[ki], c->K, c->NT, c->V, nblocks, ctl, k,
+                                   st);
 }
 
 // Persistent launch of nblocks blocks of K steps, directly or through a cached CUDA graph.
@@ -666,7 +680,8 @@ int run_steps(lbm_ctx* c, long long nsteps) {
     while (K > left) K >>= 1;  // the remainder runs with shallower launches (same arithmetic)
     const int ki = depth_index(K);
     cudaError_t e = lbm::launch_step_tiles<R>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur], c->Ntot,
-                                              lat_for(c, K), c->B, c->ntiles_k[ki], K, c->NT, c->V, k, c->stream, 0);
+                                              lat_for(c, K), tile_map_for(c, K), c->B, c->ntiles_k[ki], K, c->NT,
+                                              c->V, k, c->stream, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur = 1 - c->cur;
     left -= K;
@@ -747,6 +762,7 @@ void lbm_destroy(lbm_ctx* c) {
   dev_free(c->d_pflag);
   dev_free(c->d_stage);
   dev_free(c->d_done);
+  dev_free(c->d_tile_lat);
   dev_free(c->d_counter);
   dev_free(c->d_status);
   if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -949,11 +965,11 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
           cudaError_t e;
           if (c->precision == LBM_F64)
             e = lbm::launch_step_tiles<double>((const double*)c->state[c->cur], (double*)c->state[1 - c->cur],
-                                               c->Ntot, lat_for(c, k), c->B, nt_run, k, nt, v,
+                                               c->Ntot, lat_for(c, k), tile_map_for(c, k), c->B, nt_run, k, nt, v,
                                                make_constset<double>(c->ph), c->stream, 0);
           else
             e = lbm::launch_step_tiles<float>((const float*)c->state[c->cur], (float*)c->state[1 - c->cur],
-                                              c->Ntot, lat_for(c, k), c->B, nt_run, k, nt, v,
+                                              c->Ntot, lat_for(c, k), tile_map_for(c, k), c->B, nt_run, k, nt, v,
                                               make_constset<float>(c->ph), c->stream, 0);
           if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
         }
@@ -1079,8 +1095,9 @@ int adjoint_reverse(lbm_ctx* c, int* res) {
     std::vector<const R*> st(len);
     st[0] = (const R*)c->ckpt[j];
     for (long long i = 1; i < len; ++i) {
-      cudaError_t e = lbm::launch_step_tiles<R>(st[i - 1], (R*)c->stash[i - 1], c->Ntot, lat_for(c, 1), c->B,
-                                                c->ntiles_k[0], 1, c->NT, c->V, k, c->stream, 0);
+      cudaError_t e = lbm::launch_step_tiles<R>(st[i - 1], (R*)c->stash[i - 1], c->Ntot, lat_for(c, 1),
+                                                tile_map_for(c, 1), c->B, c->ntiles_k[0], 1, c->NT, c->V, k, c->stream,
+                                                0);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint recompute");
       st[i] = (const R*)c->stash[i - 1];
     }

@@ -51,15 +51,18 @@ struct Consts {
   int source_on;
 };
 
-// Lane arithmetic: add, sub, mul, fused multiply-add, reciprocal.
-__device__ __forceinline__ float ad(float a, float b) { return a + b; }
-__device__ __forceinline__ double ad(double a, double b) { return a + b; }
+// Lane arithmetic: add, sub, mul, fused multiply-add, reciprocal. Adds and multiplies are the
+// round-to-nearest intrinsics, which the compiler never fuses, so every fused multiply-add is an
+// explicit fm() and a node's result does not depend on how its kernel instantiation was optimised
+// (the tile shapes and depths give bitwise identical states).
+__device__ __forceinline__ float ad(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float2 ad(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float sb(float a, float b) { return a - b; }
-__device__ __forceinline__ double sb(double a, double b) { return a - b; }
+__device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float2 sb(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ float ml(float a, float b) { return a * b; }
-__device__ __forceinline__ double ml(double a, double b) { return a * b; }
+__device__ __forceinline__ float ml(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float2 ml(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
@@ -323,23 +326,28 @@ inline const Consts<float2>& ConstSet<float>::get<float2>() const { return p; }
 // Host-side launchers (lbm_step.cu). A tile has NT threads of V nodes; K steps per launch.
 // Only the first ntiles tiles are processed (the autotuner times partial launches).
 template <typename R>
-cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, int B,
+cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, const int* tile_lat, int B,
                               long long ntiles, int K, int NT, int V, const ConstSet<R>& c, cudaStream_t st,
                               long long grid_cap);
+// tile_lat[t] = lattice of tile t for a table of first tiles (lattice_of_tile, once per configuration).
+cudaError_t launch_tile_map(const LatDev* lat, int B, long long ntiles, int* map, cudaStream_t st);
 bool valid_tile_config(int K, int NT, int V, bool fp64);
+
+// Work unit of the persistent launch: kUnitTiles consecutive tiles of one time block.
+constexpr int kUnitTiles = 8;
 
 // Control block of the persistent launch (device pointers).
 struct PersistentCtl {
   unsigned long long* counter;  // next work unit
-  int* done;                    // per tile: number of finished time blocks
+  int* done;                    // per work unit: number of finished time blocks
   int* status;                  // 0, or 1 once a bounded wait has expired
   long long spin_limit;         // polls (about 100 ns apart) before a wait gives up
-  long long withhold;           // test hook: tile whose first block is never published (-1: none)
+  long long withhold;           // test hook: work unit whose first block is never published (-1: none)
 };
 template <typename R>
-cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, int B, long long ntiles, int K,
-                              int NT, int V, long long nblocks, const PersistentCtl& ctl, const ConstSet<R>& c,
-                              cudaStream_t st);
+cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, const int* tile_lat, int B,
+                              long long ntiles, int K, int NT, int V, long long nblocks, const PersistentCtl& ctl,
+                              const ConstSet<R>& c, cudaStream_t st);
 
 // Adjoint (lbm_adjoint.cu): one step per launch, tiles of kAdjointThreads nodes (halo 2 per side).
 constexpr int kAdjointThreads = 256;

@@ -24,10 +24,74 @@ __device__ __forceinline__ R ld_state(const R* p) {
   else return *p;
 }
 
-// Advances one tile K steps: reads `in`, writes the interior of the tile to `out`.
+// Loads (or stores) the six planes of a tile with fully coalesced accesses through a shared buffer of
+// NT*V elements, one plane at a time; thread t then holds (or held) nodes tV .. tV + V - 1. Used by the
+// persistent kernel, whose loads bypass L1 (other CTAs rewrite the buffers during the launch).
+// Planes staged per barrier pair: all six when they fit in 24 KB, else one at a time.
+template <typename R, int NT, int V>
+struct StagePlanes {
+  static constexpr int value = (6 * NT * V * (int)sizeof(R) <= 24576) ? 6 : 1;
+};
+
+template <typename R, int NT, int V, bool CG, bool WALLS>
+__device__ __forceinline__ void staged_load(const R* in, long long plane, long long off, long long N, long long p_first,
+                                            R* stage, R (&f)[V][6]) {
+  constexpr int PL = StagePlanes<R, NT, V>::value;
+  long long src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    long long lp = p_first + q * NT + threadIdx.x;
+    if (!WALLS) {
+      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+    } else {
+      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+    }
+    src[q] = off + lp;
+  }
+#pragma unroll
+  for (int i0 = 0; i0 < 6; i0 += PL) {
+#pragma unroll
+    for (int p = 0; p < PL; ++p)
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+        stage[p * NT * V + q * NT + threadIdx.x] = ld_state<R, CG>(in + (i0 + p) * plane + src[q]);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PL; ++p)
+#pragma unroll
+      for (int v = 0; v < V; ++v) f[v][i0 + p] = stage[p * NT * V + threadIdx.x * V + v];
+    __syncthreads();
+  }
+}
+
+template <typename R, int NT, int V>
+__device__ __forceinline__ void staged_store(R* out, long long plane, long long off, long long N, long long p_first,
+                                             int halo, int bout, R* stage, const R (&f)[V][6]) {
+  constexpr int PL = StagePlanes<R, NT, V>::value;
+#pragma unroll
+  for (int i0 = 0; i0 < 6; i0 += PL) {
+#pragma unroll
+    for (int p = 0; p < PL; ++p)
+#pragma unroll
+      for (int v = 0; v < V; ++v) stage[p * NT * V + threadIdx.x * V + v] = f[v][i0 + p];
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PL; ++p)
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int n = q * NT + threadIdx.x;
+        const long long pos = p_first + n;
+        if (n >= halo && n < halo + bout && pos < N) out[(i0 + p) * plane + off + pos] = stage[p * NT * V + n];
+      }
+    __syncthreads();
+  }
+}
+
+// Advances one tile K steps: reads `in`, writes the interior of the tile to `out`. With a shared
+// staging buffer (persistent kernel) the global accesses are coalesced through it.
 template <typename R, int NT, int V, bool CG, bool WALLS>
 __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, const LatDev& d, long long start,
-                                          int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4]) {
+                                          int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4], R* stage) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int halo = 2 * K;
@@ -43,17 +107,24 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const long long pos = pos0 + v;
-    long long lp = pos;
-    if (!WALLS) {
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-    } else {
-      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
-    }
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
-    const R* src = in + off + lp;
+  }
+  if (stage) {
+    staged_load<R, NT, V, CG, WALLS>(in, plane, off, N, start - halo, stage, f);
+  } else {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) f[v][i] = ld_state<R, CG>(src + i * plane);
+    for (int v = 0; v < V; ++v) {
+      long long lp = pos0 + v;
+      if (!WALLS) {
+        if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+      } else {
+        lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+      }
+      const R* src = in + off + lp;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) f[v][i] = ld_state<R, CG>(src + i * plane);
+    }
   }
 
   for (int k = 0; k < K; ++k) {
@@ -98,6 +169,10 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     }
   }
 
+  if (stage) {
+    staged_store<R, NT, V>(out, plane, off, N, start - halo, halo, bout, stage, f);
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int local = threadIdx.x * V + v;
@@ -116,7 +191,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 template <int NT, int V, bool CG, bool WALLS>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
-                                                 float (*e_ut)[4], float (*e_f)[4]) {
+                                                 float (*e_ut)[4], float (*e_f)[4], float* stage) {
   constexpr int NW = NT / 32, NL = V / 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int halo = 2 * K;
@@ -134,19 +209,31 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const long long pos = pos0 + v;
-    long long lp = pos;
-    if (!WALLS) {
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-    } else {
-      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
-    }
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
-    const float* src = in + off + lp;
+  }
+  if (stage) {
+    float fl[V][6];
+    staged_load<float, NT, V, CG, WALLS>(in, plane, off, N, start - halo, stage, fl);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const float x = ld_state<float, CG>(src + i * plane);
-      if (v & 1) f[v >> 1][i].y = x; else f[v >> 1][i].x = x;
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) f[l][i] = make_float2(fl[2 * l][i], fl[2 * l + 1][i]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      long long lp = pos0 + v;
+      if (!WALLS) {
+        if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+      } else {
+        lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+      }
+      const float* src = in + off + lp;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const float x = ld_state<float, CG>(src + i * plane);
+        if (v & 1) f[v >> 1][i].y = x; else f[v >> 1][i].x = x;
+      }
     }
   }
 
@@ -196,6 +283,15 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     }
   }
 
+  if (stage) {
+    float fl[V][6];
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) fl[v][i] = (v & 1) ? f[v >> 1][i].y : f[v >> 1][i].x;
+    staged_store<float, NT, V>(out, plane, off, N, start - halo, halo, bout, stage, fl);
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int local = threadIdx.x * V + v;
@@ -234,48 +330,61 @@ struct Lanes<float, 4> {
 template <typename R, int NT, int V, bool CG>
 __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                             int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
-                                            R (*e_f)[4]) {
+                                            R (*e_f)[4], R* stage = nullptr) {
   // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
   if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
-    if (d.bc == 0) tile_body_packed<NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f);
-    else tile_body_packed<NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f);
+    if (d.bc == 0) tile_body_packed<NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    else tile_body_packed<NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
   } else {
-    if (d.bc == 0) tile_body<R, NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f);
-    else tile_body<R, NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f);
+    if (d.bc == 0) tile_body<R, NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    else tile_body<R, NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
   }
+}
+
+// Lattice of every tile (one binary search per tile per configuration instead of per launch).
+__global__ void tile_map_kernel(const LatDev* __restrict__ lat, int B, long long ntiles, int* __restrict__ map) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < ntiles) map[t] = lattice_of_tile(lat, B, t);
+}
+
+cudaError_t launch_tile_map(const LatDev* lat, int B, long long ntiles, int* map, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  tile_map_kernel<<<(unsigned)((ntiles + 255) / 256), 256, 0, st>>>(lat, B, ntiles, map);
+  return cudaGetLastError();
 }
 
 template <typename R, int NT, int V>
 __global__ void __launch_bounds__(NT) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
                                                         long long plane, const LatDev* __restrict__ lat,
-                                                        int B, long long ntiles, int K,
-                                                        Consts<typename Lanes<R, V>::type> c) {
+                                                        const int* __restrict__ tile_lat, int B, long long ntiles,
+                                                        int K, Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
   const long long bout = NT * V - 4 * K;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int L = B > 1 ? lattice_of_tile(lat, B, tile) : 0;
+    const int L = B > 1 ? tile_lat[tile] : 0;
     const LatDev d = lat[L];
     tile_update<R, NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
   }
 }
 
 template <typename R, int NT, int V>
-static cudaError_t launch_nt_v(const R* in, R* out, long long plane, const LatDev* lat, int B, long long ntiles,
-                               int K, const ConstSet<R>& cs, cudaStream_t st, long long grid) {
-  step_tiles_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, B, ntiles, K,
+static cudaError_t launch_nt_v(const R* in, R* out, long long plane, const LatDev* lat, const int* tile_lat, int B,
+                               long long ntiles, int K, const ConstSet<R>& cs, cudaStream_t st, long long grid) {
+  step_tiles_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, tile_lat, B, ntiles, K,
                                                               cs.template get<typename Lanes<R, V>::type>());
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, int B, long long ntiles,
-                              int K, int NT, int V, const ConstSet<R>& c, cudaStream_t st, long long grid_cap) {
+cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev* lat, const int* tile_lat, int B,
+                              long long ntiles, int K, int NT, int V, const ConstSet<R>& c, cudaStream_t st,
+                              long long grid_cap) {
   if (ntiles <= 0) return cudaSuccess;
   long long grid = ntiles;
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
 #define LBM_CASE(nt, v) \
-  if (NT == nt && V == v) return launch_nt_v<R, nt, v>(in, out, plane, lat, B, ntiles, K, c, st, grid);
+  if (NT == nt && V == v) return launch_nt_v<R, nt, v>(in, out, plane, lat, tile_lat, B, ntiles, K, c, st, grid);
   LBM_CASE(128, 1) LBM_CASE(128, 2) LBM_CASE(128, 4)
   LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
   LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
@@ -306,63 +415,84 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 
 template <typename R, int NT, int V>
 __global__ void __launch_bounds__(NT) persistent_kernel(R* buf0, R* buf1, long long plane,
-                                                        const LatDev* __restrict__ lat, int B, long long ntiles,
+                                                        const LatDev* __restrict__ lat,
+                                                        const int* __restrict__ tile_lat, int B, long long ntiles,
                                                         int K, long long nblocks, PersistentCtl ctl,
                                                         Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
-  __shared__ long long s_unit;
+  __shared__ R stage[StagePlanes<R, NT, V>::value * NT * V];
+  __shared__ long long s_next;
   __shared__ int s_go;
-  const long long total = nblocks * ntiles;
+  const long long nunits = (ntiles + kUnitTiles - 1) / kUnitTiles;
+  const long long total = nblocks * nunits;
   const long long bout = NT * V - 4 * K;
+  if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) {
-      const long long u = (long long)atomicAdd(ctl.counter, 1ULL);
-      int go = u < total;
-      if (go && *((volatile int*)ctl.status) != 0) go = 0;
-      if (go && u >= ntiles) {
-        const long long b = u / ntiles, i = u % ntiles;
-        const int L = B > 1 ? lattice_of_tile(lat, B, i) : 0;
-        const long long t0 = lat[L].tile0;
-        const long long nt = (L + 1 < B ? lat[L + 1].tile0 : ntiles) - t0;
-        const long long li = i - t0;
-        const bool periodic = lat[L].bc == 0;
-        const long long left = li > 0 ? i - 1 : (periodic ? t0 + nt - 1 : i);
-        const long long right = li < nt - 1 ? i + 1 : (periodic ? t0 : i);
+    const long long u = s_next;
+    __syncthreads();  // every thread has read s_next before it is overwritten
+    if (u >= total) break;
+    const long long b = u / nunits, k = u % nunits;
+    if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);  // claim ahead
+    if (threadIdx.x < 32) {
+      // Lane l checks tile k * kUnitTiles + l: its own unit and the units of its lattice neighbours
+      // must have finished block b - 1.
+      // Every exit of this loop is warp-uniform: the status word is read by lane 0 and broadcast.
+      int go = __shfl_sync(0xffffffffu, threadIdx.x == 0 ? *((volatile int*)ctl.status) : 0, 0) == 0;
+      if (go && b > 0) {
+        long long uL = k, uR = k;
+        const long long i = k * kUnitTiles + threadIdx.x;
+        if (threadIdx.x < kUnitTiles && i < ntiles) {
+          const int L = B > 1 ? tile_lat[i] : 0;
+          const long long t0 = lat[L].tile0;
+          const long long nt = (L + 1 < B ? lat[L + 1].tile0 : ntiles) - t0;
+          const bool periodic = lat[L].bc == 0;
+          const long long left = i > t0 ? i - 1 : (periodic ? t0 + nt - 1 : i);
+          const long long right = i < t0 + nt - 1 ? i + 1 : (periodic ? t0 : i);
+          uL = left / kUnitTiles;
+          uR = right / kUnitTiles;
+        }
         long long spins = 0;
         for (;;) {
-          if (ld_acquire_gpu(ctl.done + left) >= b && ld_acquire_gpu(ctl.done + i) >= b &&
-              ld_acquire_gpu(ctl.done + right) >= b)
+          const bool ready = ld_acquire_gpu(ctl.done + k) >= b && ld_acquire_gpu(ctl.done + uL) >= b &&
+                             ld_acquire_gpu(ctl.done + uR) >= b;
+          if (__all_sync(0xffffffffu, ready)) break;
+          const int st = __shfl_sync(0xffffffffu, threadIdx.x == 0 ? *((volatile int*)ctl.status) : 0, 0);
+          if (st != 0) { go = 0; break; }
+          if (++spins > ctl.spin_limit) {
+            if (threadIdx.x == 0) atomicExch(ctl.status, 1);
+            go = 0;
             break;
-          if (*((volatile int*)ctl.status) != 0) { go = 0; break; }
-          if (++spins > ctl.spin_limit) { atomicExch(ctl.status, 1); go = 0; break; }
+          }
           __nanosleep(100);
         }
       }
-      s_unit = u;
-      s_go = go;
+      if (threadIdx.x == 0) s_go = go;
     }
     __syncthreads();
-    const long long u = s_unit;
     if (!s_go) break;
-    const long long b = u / ntiles, i = u % ntiles;
-    const int L = B > 1 ? lattice_of_tile(lat, B, i) : 0;
-    const LatDev d = lat[L];
-    const bool withheld = (b == 0 && i == ctl.withhold);
-    if (!withheld)
-      tile_update<R, NT, V, true>((b & 1) ? buf1 : buf0, (b & 1) ? buf0 : buf1, plane, d, (i - d.tile0) * bout, K, c,
-                                  e_ut, e_f);
+    const bool withheld = (b == 0 && k == ctl.withhold);
+    if (!withheld) {
+      R* in = (b & 1) ? buf1 : buf0;
+      R* out = (b & 1) ? buf0 : buf1;
+      for (long long i = k * kUnitTiles; i < (k + 1) * kUnitTiles && i < ntiles; ++i) {
+        const int L = B > 1 ? tile_lat[i] : 0;
+        const LatDev d = lat[L];
+        tile_update<R, NT, V, true>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, stage);
+      }
+    }
     __syncthreads();
     if (threadIdx.x == 0 && !withheld) {
       __threadfence();
-      st_release_gpu(ctl.done + i, (int)(b + 1));
+      st_release_gpu(ctl.done + k, (int)(b + 1));
     }
   }
 }
 
 template <typename R, int NT, int V>
-static cudaError_t launch_persistent_nt_v(R* buf0, R* buf1, long long plane, const LatDev* lat, int B,
-                                          long long ntiles, int K, long long nblocks, const PersistentCtl& ctl,
+static cudaError_t launch_persistent_nt_v(R* buf0, R* buf1, long long plane, const LatDev* lat, const int* tile_lat,
+                                          int B, long long ntiles, int K, long long nblocks, const PersistentCtl& ctl,
                                           const ConstSet<R>& cs, cudaStream_t st) {
   const auto c = cs.template get<typename Lanes<R, V>::type>();
   int dev = 0, nsm = 0, per_sm = 0;
@@ -370,20 +500,21 @@ static cudaError_t launch_persistent_nt_v(R* buf0, R* buf1, long long plane, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<R, NT, V>, NT, 0);
   long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
-  const long long total = nblocks * ntiles;
+  const long long total = nblocks * ((ntiles + kUnitTiles - 1) / kUnitTiles);
   if (grid > total) grid = total;
-  persistent_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(buf0, buf1, plane, lat, B, ntiles, K, nblocks, ctl, c);
+  persistent_kernel<R, NT, V><<<(unsigned)grid, NT, 0, st>>>(buf0, buf1, plane, lat, tile_lat, B, ntiles, K, nblocks,
+                                                              ctl, c);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, int B, long long ntiles, int K,
-                              int NT, int V, long long nblocks, const PersistentCtl& ctl, const ConstSet<R>& c,
-                              cudaStream_t st) {
+cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* lat, const int* tile_lat, int B,
+                              long long ntiles, int K, int NT, int V, long long nblocks, const PersistentCtl& ctl,
+                              const ConstSet<R>& c, cudaStream_t st) {
   if (ntiles <= 0 || nblocks <= 0) return cudaSuccess;
 #define LBM_CASE(nt, v)       \
   if (NT == nt && V == v) \
-    return launch_persistent_nt_v<R, nt, v>(buf0, buf1, plane, lat, B, ntiles, K, nblocks, ctl, c, st);
+    return launch_persistent_nt_v<R, nt, v>(buf0, buf1, plane, lat, tile_lat, B, ntiles, K, nblocks, ctl, c, st);
   LBM_CASE(128, 1) LBM_CASE(128, 2) LBM_CASE(128, 4)
   LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
   LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
@@ -393,11 +524,12 @@ cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* l
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_persistent<float>(float*, float*, long long, const LatDev*, int, long long, int, int, int,
-                                              long long, const PersistentCtl&, const ConstSet<float>&, cudaStream_t);
-template cudaError_t launch_persistent<double>(double*, double*, long long, const LatDev*, int, long long, int, int,
-                                               int, long long, const PersistentCtl&, const ConstSet<double>&,
-                                               cudaStream_t);
+template cudaError_t launch_persistent<float>(float*, float*, long long, const LatDev*, const int*, int, long long,
+                                              int, int, int, long long, const PersistentCtl&, const ConstSet<float>&,
+                                              cudaStream_t);
+template cudaError_t launch_persistent<double>(double*, double*, long long, const LatDev*, const int*, int, long long,
+                                               int, int, int, long long, const PersistentCtl&,
+                                               const ConstSet<double>&, cudaStream_t);
 
 bool valid_tile_config(int K, int NT, int V, bool fp64) {
   const bool nt_ok = NT == 128 || NT == 256 || NT == 512 || NT == 1024;
@@ -408,9 +540,11 @@ bool valid_tile_config(int K, int NT, int V, bool fp64) {
   return nt_ok && v_ok && k_ok && size_ok && NT * V - 4 * K >= 32;
 }
 
-template cudaError_t launch_step_tiles<float>(const float*, float*, long long, const LatDev*, int, long long, int,
-                                              int, int, const ConstSet<float>&, cudaStream_t, long long);
-template cudaError_t launch_step_tiles<double>(const double*, double*, long long, const LatDev*, int, long long,
-                                               int, int, int, const ConstSet<double>&, cudaStream_t, long long);
+template cudaError_t launch_step_tiles<float>(const float*, float*, long long, const LatDev*, const int*, int,
+                                              long long, int, int, int, const ConstSet<float>&, cudaStream_t,
+                                              long long);
+template cudaError_t launch_step_tiles<double>(const double*, double*, long long, const LatDev*, const int*, int,
+                                               long long, int, int, int, const ConstSet<double>&, cudaStream_t,
+                                               long long);
 
 }  // namespace lbm

@@ -399,9 +399,11 @@ def test_precision_sweep_amplitude_02(O, lbm):
 def test_linear_variant_section7(O, lbm, u0, s0, precision, tol):
     """The section 7 scheme (linear equilibria of eq. (equilibres-NS-linearise) around (rho0, u0,
     s0), sigma_eps = 1.5, no source) on small acoustic waves (figure 1 amplitude, delta = 1e-3) in
-    two lattices (periodic, and bounce-back at rest): GPU against the oracle's linear mode."""
+    two lattices (periodic, and bounce-back when u0 = 0; at u0 != 0 walls contradict the
+    linearisation velocity and amplify rounding about 1000-fold over the run, so both are periodic
+    there): GPU against the oracle's linear mode."""
     lengths = np.array([4099, 777])
-    bcs = np.array([0, 1])
+    bcs = np.array([0, 1 if u0 == 0 else 0])
     s_e = 1.9
     rates = O.linear_rates(s_e)
     phys = dict(equilibria=1, u0_lin=u0, s0_lin=s0, source_on=0)

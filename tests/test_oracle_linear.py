@@ -77,3 +77,46 @@ def test_linear_variant_requires_lattice_units(O):
     with pytest.raises(ValueError):
         ph = O.default_phys(eq_mode=1, lam=2.0)
         O.run(ph, O.linear_rates(1.5), np.zeros((8, 6)), 1)
+
+
+def _printed_Q(u0, s0, c02, g=1.4):
+    """Coefficients of eq. (equilibres-NS-linearise) on (rho, J, zeta) (lambda = c_p = 1)."""
+    return np.array([
+        [3 * (1 - s0) * c02 - 3 * u0 ** 2 - 2, 6 * u0, 3 * u0 ** 2],
+        [-u0 * s0, s0, u0],
+        [-3 * (s0 * s0 * c02) - 6 * s0 * u0 ** 2 + 3 * s0 * c02 + 2 - 2 * s0 - 2 / g, 6 * u0 * s0,
+         3 * (u0 ** 2 + s0 * c02)]])
+
+
+@pytest.mark.parametrize("u0,s0", [(0.0, 0.0), (0.15, 0.2), (0.1, -0.3), (-0.05, 0.4)])
+def test_linear_variant_second_order_damping(O, u0, s0):
+    """Second-order equivalent equations of a linear scheme, eq. (edp-ordre-2) with the defects of
+    eq. (thetas): with m_eq = Q W on the non-conserved moments, A = Lam_WW + Lam_WN Q and
+    D = dt Lam_WN diag(sigma) (Lam_NW + Lam_NN Q - Q A); a conserved mode (right/left eigenvectors
+    r, l of A) decays at l D r / (l r). Lambda is the printed eq. (Lambda-d1q3q3) (tests/golden),
+    Q the printed linear equilibria; the decay rates are compared with the oracle's exact Jacobian."""
+    from conftest import read_symbolic_matrix
+
+    ph = _ph(O, u0, s0)
+    r = O.linear_rates(1.5)
+    c02 = 1.4 * ph.p0 / ph.rho0
+    Lam = read_symbolic_matrix("Lambda_d1q3q3.txt", l=1.0)   # order (rho, J, zeta, e, psi, eps)
+    W, Nn = [0, 1, 2], [3, 4, 5]
+    Q = _printed_Q(u0, s0, c02)
+    A = Lam[np.ix_(W, W)] + Lam[np.ix_(W, Nn)] @ Q
+    sig = np.diag(1 / r - 0.5)
+    D = 1.0 * Lam[np.ix_(W, Nn)] @ sig @ (Lam[np.ix_(Nn, W)] + Lam[np.ix_(Nn, Nn)] @ Q - Q @ A)
+    w, Rv = np.linalg.eig(A)
+    Lv = np.linalg.inv(Rv)
+    pred = {}
+    for i in range(3):
+        pred[np.real(w[i])] = np.real(Lv[i] @ D @ Rv[:, i])
+    B = L.jacobian_blocks(ph, r, 1.0, u0, s0)
+    th = 2e-3
+    mu = L.conserved_modes(L.symbol(B, th))
+    speeds = -np.angle(mu) / th
+    damps = -np.log(np.abs(mu)) / th ** 2
+    for sp, dm in zip(speeds, damps):
+        key = min(pred, key=lambda v: abs(v - sp))
+        assert abs(key - sp) < 1e-4
+        assert abs(dm - pred[key]) <= 1e-3 * abs(pred[key]) + 1e-6, (sp, dm, pred[key])

@@ -27,6 +27,15 @@ MUTANTS = {
     "wall ghost velocity": ("if (j == 0) { ul = -u; Tl = T; }", "if (j == 0) { ul = u; Tl = T; }"),
     "stream wrap swapped": ("else if (ph.bc == 0) { out[1] = fs[1]; out[4] = fs[4]; }",
                             "else if (ph.bc == 0) { out[2] = fs[1]; out[5] = fs[4]; }"),
+    "linear e_eq J coefficient": ("+ 6.0 * u0 * J + 3.0 * (u0 * u0 / cp) * zeta;",
+                                  "+ 3.0 * u0 * J + 3.0 * (u0 * u0 / cp) * zeta;"),
+    "linear psi_eq sign": ("psi_eq = -u0 * s0 * rho + s0 * J + u0 * zeta;",
+                           "psi_eq = u0 * s0 * rho + s0 * J + u0 * zeta;"),
+    "linear e_eq rho coefficient": ("(3.0 * (1.0 - s0 / cp) * c02 - 3.0 * u0 * u0 - 2.0 * l2) * rho",
+                                    "(3.0 * (1.0 - s0 / cp) * c02 - 2.0 * l2) * rho"),
+    "linear eps_eq rho constant": ("+ 3.0 * s0 * c02 + 2.0 - 2.0 * s0 - 2.0 / g) * rho",
+                                   "+ 3.0 * s0 * c02 + 2.0 - 2.0 * s0) * rho"),
+    "linear eps_eq zeta coefficient": ("3.0 * (cp * u0 * u0 + s0 * c02) * zeta;", "3.0 * (cp * u0 * u0) * zeta;"),
 }
 
 
@@ -42,6 +51,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                     "-o", str(lib), str(mut)], check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_linear.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
