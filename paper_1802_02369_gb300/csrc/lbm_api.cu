@@ -586,6 +586,10 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
     }
     d.bc = bc[b];
     d.pad = 0;
+    {
+      const double v[8] = {d.s_e, d.s_psi, d.s_eps, d.q_src, d.s0h, d.lin_e0, d.lin_p0, d.lin_q0};
+      for (int i = 0; i < 8; ++i) d.f32[i] = (float)v[i];  // round to nearest, as the device conversion
+    }
     tot += N[b];
   }
   c->offset[B] = tot;

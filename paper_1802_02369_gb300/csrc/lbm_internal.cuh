@@ -21,7 +21,22 @@ struct LatDev {
   double s0h;      // s0 / c_p
   double lin_e0, lin_p0, lin_q0;  // constant terms of the linear equilibria in scaled moments
   int bc, pad;
+  // s_e, s_psi, s_eps, q_src, s0h, lin_e0, lin_p0, lin_q0 rounded to FP32 on the host, for the FP32
+  // kernels (a double-to-float conversion on the device runs on the slow FP64 pipe).
+  float f32[8];
 };
+
+// The per-lattice parameters of the step kernels in the arithmetic type R.
+template <typename R>
+struct StepParams {
+  R s_e, s_psi, s_eps, q_src, s0h, lin_e0, lin_p0, lin_q0;
+};
+__device__ __forceinline__ StepParams<double> step_params(const LatDev& d, double) {
+  return {d.s_e, d.s_psi, d.s_eps, d.q_src, d.s0h, d.lin_e0, d.lin_p0, d.lin_q0};
+}
+__device__ __forceinline__ StepParams<float> step_params(const LatDev& d, float) {
+  return {d.f32[0], d.f32[1], d.f32[2], d.f32[3], d.f32[4], d.f32[5], d.f32[6], d.f32[7]};
+}
 
 // Constants shared by all lattices, converted on the host to the lane type X the node arithmetic
 // runs in: double, float, or float2 (two nodes per lane for Blackwell's paired FP32 instructions;
@@ -60,7 +75,9 @@ __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b
 __device__ __forceinline__ float2 ad(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float2 sb(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a - b as a + b * (-1): the product is exact, so this is the correctly rounded difference in one
+// paired instruction (negating both halves of b would take two more).
+__device__ __forceinline__ float2 sb(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float ml(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float2 ml(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -87,8 +104,9 @@ __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
 
 __device__ __forceinline__ float2 atanh2_series(float2 t) {  // 2 atanh(t / (2 + t)) for |t| <= 0.5
   const float2 d = __fadd2_rn(t, make_float2(2.0f, 2.0f));
+  const float2 nd = __ffma2_rn(t, make_float2(-1.0f, -1.0f), make_float2(-2.0f, -2.0f));  // -d
   float2 y = m_rcp(d);
-  y = __ffma2_rn(y, __ffma2_rn(make_float2(-d.x, -d.y), y, make_float2(1.0f, 1.0f)), y);  // Newton step
+  y = __ffma2_rn(y, __ffma2_rn(nd, y, make_float2(1.0f, 1.0f)), y);  // Newton step
   const float2 z = __fmul2_rn(t, y);
   const float2 w = __fmul2_rn(z, z);
   float2 p = make_float2(1.0f / 11.0f, 1.0f / 11.0f);

@@ -97,9 +97,10 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
   const int halo = 2 * K;
   const int bout = NT * V - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const R s_e = R(d.s_e), s_psi = R(d.s_psi), s_eps = R(d.s_eps), q_src = R(d.q_src), s0h = R(d.s0h);
+  const StepParams<R> P = step_params(d, R{});
+  const R s_e = P.s_e, s_psi = P.s_psi, s_eps = P.s_eps, q_src = P.q_src, s0h = P.s0h;
   const R m_s0h = -s0h;
-  const R le0 = R(d.lin_e0), lp0 = R(d.lin_p0), lq0 = R(d.lin_q0);
+  const R le0 = P.lin_e0, lp0 = P.lin_p0, lq0 = P.lin_q0;
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   R f[V][6];
@@ -197,11 +198,12 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   const int halo = 2 * K;
   const int bout = NT * V - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const float2 s_e = make_float2((float)d.s_e, (float)d.s_e), s_psi = make_float2((float)d.s_psi, (float)d.s_psi);
-  const float2 s_eps = make_float2((float)d.s_eps, (float)d.s_eps), q_src = make_float2((float)d.q_src, (float)d.q_src);
-  const float2 s0h = make_float2((float)d.s0h, (float)d.s0h), m_s0h = make_float2(-(float)d.s0h, -(float)d.s0h);
-  const float2 le0 = make_float2((float)d.lin_e0, (float)d.lin_e0), lp0 = make_float2((float)d.lin_p0, (float)d.lin_p0);
-  const float2 lq0 = make_float2((float)d.lin_q0, (float)d.lin_q0);
+  const StepParams<float> P = step_params(d, 0.0f);
+  const float2 s_e = make_float2(P.s_e, P.s_e), s_psi = make_float2(P.s_psi, P.s_psi);
+  const float2 s_eps = make_float2(P.s_eps, P.s_eps), q_src = make_float2(P.q_src, P.q_src);
+  const float2 s0h = make_float2(P.s0h, P.s0h), m_s0h = make_float2(-P.s0h, -P.s0h);
+  const float2 le0 = make_float2(P.lin_e0, P.lin_e0), lp0 = make_float2(P.lin_p0, P.lin_p0);
+  const float2 lq0 = make_float2(P.lin_q0, P.lin_q0);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
   float2 f[NL][6];
@@ -353,8 +355,11 @@ cudaError_t launch_tile_map(const LatDev* lat, int B, long long ntiles, int* map
   return cudaGetLastError();
 }
 
+// 128 threads of four FP32 nodes: at least eight resident CTAs per SM, i.e. at most 64 registers
+// (measured faster than the 80-90 the compiler picks otherwise). A minimum of 0 leaves the other
+// instances to the compiler's own choice (an explicit 1 lets it take far more registers).
 template <typename R, int NT, int V>
-__global__ void __launch_bounds__(NT) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 8 : 0) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
                                                         long long plane, const LatDev* __restrict__ lat,
                                                         const int* __restrict__ tile_lat, int B, long long ntiles,
                                                         int K, Consts<typename Lanes<R, V>::type> c) {
