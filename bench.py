@@ -36,7 +36,17 @@ WORKLOAD = "steepening acoustic wave, single periodic lattice N=2^26, lambda=1, 
 # dram__bytes_write.sum) on the same workload at N = 2^23 and scaled to a full launch by the node
 # count (traffic is proportional to the nodes); keyed by (precision, k, block_threads,
 # nodes_per_thread) of the current kernel version. Summaries: profiles/step_tiles_*.md.
-TRAFFIC_BYTES_PER_NODE = {("f32", 8, 256, 2): (201.381632e6 + 149.676544e6) / 8388608}
+# Arithmetic per node-update for the ALU roofline (halo recomputation excluded). FP32: the scaled node
+# update as the step kernel implements it (moments, equation of state with the series log1p and
+# expm1, equilibria, relaxation, source, M^-1): 19 add/sub + 22 mul + 37 fma (2 flops) + 3 reciprocals
+# (1 flop) = 118 flops. FP64: the kernel's executed FP64 arithmetic per node-update, CUDA's log1p and
+# expm1 included, from ncu at (1, 256, 2), N = 2^23: (2 DFMA + DADD + DMUL) / nodes.
+FLOPS_PER_NODE = {"f32": 118.0, "f64": (2 * 507.31008e6 + 194.468864e6 + 194.468864e6) / 8388608}
+# Peak arithmetic per SM per clock from the unit counts: 128 FP32 FMA lanes (256 flops); FP64 at
+# 2 FMA per SM per clock (4 flops; the nominal 1.25 TFLOP/s of the part at 152 SMs, 2.07 GHz).
+FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
+TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.499136e6 + 147.712768e6) / 8388608,
+                          ("f64", 1, 256, 2): (403.403008e6 + 347.594752e6) / 8388608}
 
 
 def measured_peaks():
@@ -389,6 +399,18 @@ def run_ours(args, rank: int, world: int, local: int, dist):
         cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first 2^22 nodes of the workload (periodic), {st} steps, {dt:.1f} s, FP64"}
 
+    props = torch.cuda.get_device_properties(local)
+    sm_clock_mhz = clocks.get("sm_max_mhz") or 2070.0
+
+    def roof_alu(r, prec):
+        tb = TRAFFIC_BYTES_PER_NODE.get((prec, r["k"], r["block_threads"], r["nodes_per_thread"]))
+        achieved = r["value"] / world * FLOPS_PER_NODE[prec] / 1e3          # TFLOP/s
+        peak = props.multi_processor_count * FLOPS_PER_SM_CLOCK[prec] * sm_clock_mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None if tb is None else tb * N_NODES, "flops_per_node_update": FLOPS_PER_NODE[prec],
+                "peak_kind": f"derived: {props.multi_processor_count} SMs x {FLOPS_PER_SM_CLOCK[prec]:.0f} "
+                             f"{prec.upper()} flops/clock x {sm_clock_mhz:.0f} MHz"}
+
     def roof(r, prec):
         tb = TRAFFIC_BYTES_PER_NODE.get((prec, r["k"], r["block_threads"], r["nodes_per_thread"]))
         return {"bound": "hbm", "achieved": r["achieved"], "peak": hbm_peak, "unit": "GB/s",
@@ -407,10 +429,11 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                        "nodes_per_thread": f32["nodes_per_thread"],
                        "l2": "inputs larger than L2 (FP32 state 1.6 GB, FP64 3.2 GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof(f32, "f32"),
+            "roofline": roof_alu(f32, "f32"), "roofline_hbm": roof(f32, "f32"),
             "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                      "steps_per_launch": f64["k"], "block_threads": f64["block_threads"],
-                     "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof(f64, "f64")},
+                     "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
+                     "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
