@@ -55,3 +55,43 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_linear.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
+
+
+FD_SRC = os.path.join(ROOT, "oracle", "fd_oracle.cpp")
+
+FD_MUTANTS = {
+    "fd convective difference missing 2": ("out[3 * j + 0] = Wj[0] - dt * (Fr[0] - Fl[0]) / (2.0 * dx);",
+                                           "out[3 * j + 0] = Wj[0] - dt * (Fr[0] - Fl[0]) / (dx);"),
+    "fd momentum flux drops p": ("const double Fr[3] = {Wr[1], Wr[0] * u[r] * u[r] + p[r], Wr[2] * u[r]};",
+                                 "const double Fr[3] = {Wr[1], Wr[0] * u[r] * u[r], Wr[2] * u[r]};"),
+    "fd entropy flux uses J": ("const double Fl[3] = {Wl[1], Wl[0] * u[l] * u[l] + p[l], Wl[2] * u[l]};",
+                               "const double Fl[3] = {Wl[1], Wl[0] * u[l] * u[l] + p[l], Wl[1] * u[l]};"),
+    "fd viscosity face not averaged": ("const double phiJ_r = 0.5 * (aj + ar) * (u[r] - u[j]) / dx;",
+                                       "const double phiJ_r = aj * (u[r] - u[j]) / dx;"),
+    "fd kappa drops Pr": ("const double kl = Wl[0] * ph.nu * ph.cp / ph.Pr, kj = Wj[0] * ph.nu * ph.cp / ph.Pr,",
+                          "const double kl = Wl[0] * ph.nu * ph.cp, kj = Wj[0] * ph.nu * ph.cp / ph.Pr,"),
+    "fd heat flux over T squared": ("const double bl = kl / T[l], bj = kj / T[j], br = kr / T[r];",
+                                    "const double bl = kl / T[l], bj = kj / (T[j] * T[j]), br = kr / T[r];"),
+    "fd source thermal term over T": ("kj / (T[j] * T[j]) * dTdx * dTdx;", "kj / T[j] * dTdx * dTdx;"),
+    "fd source halved": ("out[3 * j + 2] = Wj[2] - dt * (Fr[2] - Fl[2]) / (2.0 * dx) + dt * (phiZ_r - phiZ_l) / dx + dt * S;",
+                         "out[3 * j + 2] = Wj[2] - dt * (Fr[2] - Fl[2]) / (2.0 * dx) + dt * (phiZ_r - phiZ_l) / dx + 0.5 * dt * S;"),
+    "fd EOS exponent": ("std::exp(ph.gamma * (s - ph.s0) / ph.cp)", "std::exp((s - ph.s0) / ph.cp)"),
+    "fd viscous term sign": ("+ dt * (phiJ_r - phiJ_l) / dx;", "- dt * (phiJ_r - phiJ_l) / dx;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FD_MUTANTS))
+def test_fd_pins_catch_planted_mistake(name, tmp_path):
+    old, new = FD_MUTANTS[name]
+    src = open(FD_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not found exactly once"
+    mut = tmp_path / "fd_mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libfd_mutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-o", str(lib), str(mut)], check=True)
+    env = dict(os.environ, FD_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_fd.py")],
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
