@@ -317,6 +317,65 @@ def run_adjoint(args, lbm, torch):
     return out
 
 
+# Finite-difference comparison solver (section 9) on the same steepening wave: dx = 1, nu = the
+# lattice Boltzmann viscosity at s_e = 1.2 in lattice units (sigma_e lambda dx = 1/3), dt = 1 (one
+# lattice time step), source on. Bytes per node per launch: three words read and written.
+FD_NU = 1.0 / S_E - 0.5
+FD_DT = 1.0
+FD_BYTES_PER_NODE = {"f32": 24, "f64": 48}
+# Executed arithmetic per computed node-step of the finite-difference kernel (CUDA's log1p, expm1 and
+# reciprocals included), from ncu instruction counts of one launch at N = 2^23 (2 FMA + ADD + MUL over
+# the tiles' node-steps, halo included): FP64 at (4, 256, 1) 2 x 1,835,804,672 DFMA + 762,032,128 DADD
+# + 762,032,128 DMUL over 33,826 x 256 x 4 node-steps = 150.0; FP32 at (8, 256, 2) 2 x 2,216,820,736
+# FFMA + 1,177,686,016 FADD + 1,662,615,552 FMUL over 16,913 x 512 x 8 = 105.0. Per output node-update
+# this is multiplied by the tile's computed / stored nodes, NT V / (NT V - 2K).
+FD_FLOPS_PER_COMPUTED = {"f64": 5195673600 / 34637824, "f32": 7273943040 / 69275648}
+
+
+def run_fd(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
+    """Forward-Euler centred finite differences of eq. (NS-rho-J-zeta) on the benchmark wave,
+    FP64 and FP32, autotuned (or the fixed --fd-config)."""
+    rho, u, p = workload_fields(N)
+    d_rho, d_u = torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()
+    d_s = torch.zeros(N, dtype=torch.float64, device="cuda")   # adiabatic: p = p0 rho^gamma, s = 0
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    out = {}
+    for prec in args.precisions.split(","):
+        steps = args.fd_steps_f64 if prec == "f64" else args.fd_steps_f32
+        g = lbm.FdGrid(N, 1.0, FD_DT, FD_NU, precision=prec)
+        g.set_state(d_rho, d_u, d_s)
+        if args.fd_config:
+            g.set_config(*[int(x) for x in args.fd_config.split(",")])
+            k, nt, v = g.get_config()
+        else:
+            k, nt, v = g.autotune(2)
+        g.set_state(d_rho, d_u, d_s)
+        steps = max(k, (steps // k) * k)
+        ms = time_device(g, torch, steps, 3 * k, None, 1)
+        _, flags, _ = g.diagnostics()
+        g.close()
+        glups = N * steps / (ms * 1e-3) / 1e9
+        launch_ms = ms / (steps // k)
+        achieved = N * FD_BYTES_PER_NODE[prec] / (launch_ms * 1e-3) / 1e9
+        r = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": k, "block_threads": nt,
+             "nodes_per_thread": v, "launch_ms": launch_ms, "flags": int(flags),
+             "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": achieved / hbm_peak,
+                              "effective_gbs": glups * FD_BYTES_PER_NODE[prec],
+                              "algorithmic_bytes_per_launch": N * FD_BYTES_PER_NODE[prec]}}
+        fl = FD_FLOPS_PER_COMPUTED[prec] * nt * v / (nt * v - 2 * k)
+        a = glups * fl / 1e3
+        pk = props.multi_processor_count * FLOPS_PER_SM_CLOCK[prec] * sm_clock_mhz * 1e6 / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                         "flops_per_node_update": fl,
+                         "peak_kind": f"derived: {props.multi_processor_count} SMs x {FLOPS_PER_SM_CLOCK[prec]:.0f} "
+                                      f"{prec.upper()} flops/clock x {sm_clock_mhz:.0f} MHz"}
+        out[prec] = r
+    del d_rho, d_u, d_s
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank: int, world: int, local: int, dist):
     import torch
 
@@ -325,6 +384,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     torch.cuda.set_device(local)
     build.build()
     hbm_peak, peak_kind = measured_peaks()
+    if args.fd_only:
+        with ClockSampler(local) as clk:
+            fd = run_fd(args, lbm, torch, args.nodes, hbm_peak, 2070.0)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "finite differences", "nodes": args.nodes,
+                              "results": fd, "clocks": clk.summary()}), flush=True)
+        return
     NN = args.nodes
     rho, u, p = workload_fields(NN)
     d_rho, d_u, d_p = (torch.from_numpy(x).cuda() for x in (rho, u, p))
@@ -386,6 +452,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     batched = None if args.no_batched else run_batched(args, lbm, torch, hbm_peak, world)
     linear = None if args.no_linear else run_linear(args, lbm, torch)
     adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch)
+    fdiff = None if args.no_fd else run_fd(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
 
     if rank != 0:
         return
@@ -435,6 +502,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
                      "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
+            "finite_differences": fdiff,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
     print(json.dumps(line), flush=True)
@@ -458,6 +526,11 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps-f32", type=int, default=4000)
     ap.add_argument("--adjoint-steps-f64", type=int, default=1000)
+    ap.add_argument("--no-fd", action="store_true")
+    ap.add_argument("--fd-only", action="store_true", help="only the finite-difference leg at --nodes")
+    ap.add_argument("--fd-config", default="", help="k,block_threads,nodes_per_thread of the finite-difference kernel")
+    ap.add_argument("--fd-steps-f64", type=int, default=200)
+    ap.add_argument("--fd-steps-f32", type=int, default=1000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -224,6 +224,57 @@ int lbm_adjoint_release(lbm_ctx *ctx);
 int lbm_diagnostics_noalloc(const double *fd, int64_t N, double lambda, const lbm_phys *phys, double *sums,
                             int32_t *flags, void *stream);
 
+/* ------------------------------------------------------------------------------------------------
+ * Finite-difference comparison solver (section 9). The paper checks its lattice Boltzmann results
+ * against a finite-difference program for the (rho, J, zeta) system of eq. (NS-rho-J-zeta) with
+ * second-order centred differences in space and explicit first-order time steps. The stencil is not
+ * printed; the one built here is in conservation form on a periodic grid of N nodes:
+ *   W = (rho, J, zeta), u = J/rho, s = zeta/rho, p and T from eq. (gaz-parfait);
+ *   W_j(t + dt) = W_j - dt/(2 dx) (F_{j+1} - F_{j-1}) + dt/dx (Phi_{j+1/2} - Phi_{j-1/2}) + dt (0, 0, S_j),
+ *   F = (J, rho u^2 + p, zeta u), Phi_{j+1/2} = (0, a (u_{j+1} - u_j)/dx, b (T_{j+1} - T_j)/dx) with
+ *   a, b the means over nodes j, j+1 of rho nu and kappa/T, kappa = rho nu c_p / Pr, and the entropy
+ *   production S = (rho nu/T)(d_x u)^2 + (kappa/T^2)(d_x T)^2 from centred derivatives (the
+ *   differences of step (vii) of section 8); S is dropped when phys->source_on = 0.
+ * The sums of rho and J are conserved exactly (up to rounding); the sum of zeta grows by dt sum S.
+ * Explicit centred differences are stable only for dt <= 2 nu / (|u| + c)^2 and dt <= dx^2 / (2 nu)
+ * (roughly); the caller chooses dt. Same status codes, pointer and stream conventions as above. */
+typedef struct lbm_fd_ctx lbm_fd_ctx;
+
+/* N >= 3 periodic nodes of spacing dx > 0, time step dt > 0, kinematic viscosity nu >= 0.
+ * precision: LBM_F64, or LBM_F32_SHIFTED (FP32 storage and arithmetic of (rho - rho0, J, zeta - rho0 s0)).
+ * phys: gamma, Pr, c_p, rho0, p0, s0 and source_on of eq. (gaz-parfait) and eq. (NS-rho-J-zeta);
+ * NULL selects the section 9 values (gamma = 1.4, Pr = 1, c_p = 1, rho0 = 1, s0 = 0, source on) with
+ * p0 = rho0 c0^2 / gamma, c0 = 1/2; p0 <= 0 selects that p0 too. phys->equilibria must be 0. */
+int lbm_fd_create(lbm_fd_ctx **out, int64_t N, double dx, double dt, double nu, int32_t precision,
+                  const lbm_phys *phys, void *stream);
+void lbm_fd_destroy(lbm_fd_ctx *ctx);
+const char *lbm_fd_last_error(const lbm_fd_ctx *ctx);
+int64_t lbm_fd_steps_done(const lbm_fd_ctx *ctx);
+/* State from per-node rho, u and specific entropy s (N float64 each, host or device); resets the
+ * step counter. */
+int lbm_fd_set_state(lbm_fd_ctx *ctx, const double *rho, const double *u, const double *s);
+/* State from the conserved fields W, plane-major [3][N] float64 (rho, J, zeta), host or device. */
+int lbm_fd_set_fields(lbm_fd_ctx *ctx, const double *W);
+/* Advances nsteps >= 0 time steps of size dt (enqueued; no synchronisation). */
+int lbm_fd_step(lbm_fd_ctx *ctx, int64_t nsteps);
+/* rho, J, zeta per node into caller arrays of N float64 (host or device; any may be NULL). */
+int lbm_fd_fields(lbm_fd_ctx *ctx, double *rho, double *J, double *zeta);
+/* FP64 sums (host sums[4]: sum rho, sum J, sum zeta, sum of p/(gamma-1) + rho u^2/2) and flag bits
+ * (host flags[1]: bit 0 non-finite field, bit 1 rho <= 0, bit 2 T <= 0) in a fixed reduction order;
+ * synchronises; LBM_ERR_UNSTABLE if a flag is set (outputs still filled). */
+int lbm_fd_diagnostics(lbm_fd_ctx *ctx, double *sums, int32_t *flags);
+/* Kernel configuration: steps_per_launch k in 1..16 (temporal blocking, k halo nodes per tile side),
+ * block_threads in {128, 256, 512}, nodes_per_thread in {1, 2, 4}, with block_threads *
+ * nodes_per_thread - 2k >= 32. 0 keeps the current value. Results do not depend on it beyond
+ * rounding of contracted multiply-adds. Default 4, 256, 2. */
+int lbm_fd_set_config(lbm_fd_ctx *ctx, int32_t steps_per_launch, int32_t block_threads, int32_t nodes_per_thread);
+int lbm_fd_get_config(const lbm_fd_ctx *ctx, int32_t *steps_per_launch, int32_t *block_threads,
+                      int32_t *nodes_per_thread);
+/* Times every valid configuration on the current state (left unchanged; each trial writes only the
+ * spare buffer, over at most 16384 tiles) and keeps the fastest per node-update. trials >= 1 timed
+ * launches per candidate. Synchronises. Needs a state. */
+int lbm_fd_autotune(lbm_fd_ctx *ctx, int32_t trials);
+
 #ifdef __cplusplus
 }
 #endif

@@ -352,6 +352,12 @@ __global__ void __launch_bounds__(256) diag_final_kernel(const double* __restric
 
 }  // namespace
 
+namespace lbm {
+void* device_alloc(size_t bytes, cudaStream_t st) { return dev_alloc(bytes, st); }
+void device_free(void* p) { dev_free(p); }
+bool is_device_pointer(const void* p) { return is_device_ptr(p); }
+}  // namespace lbm
+
 // ---------------------------------------------------------------------------------------------
 // Context.
 

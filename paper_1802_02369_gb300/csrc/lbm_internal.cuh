@@ -383,4 +383,10 @@ template <typename R>
 cudaError_t launch_misfit_seed(const R* fT, const double* target, const double* rho_b, long long plane, double rho0,
                                R* aT, double* part, double* loss, cudaStream_t st);
 
+// Device memory through the allocator installed with lbm_set_allocator (cudaMalloc/cudaFree if none),
+// and the host/device test of the per-node array arguments (lbm_api.cu).
+void* device_alloc(size_t bytes, cudaStream_t st);
+void device_free(void* p);
+bool is_device_pointer(const void* p);
+
 }  // namespace lbm

@@ -112,6 +112,18 @@ def load_library(path: str = LIB_PATH):
             "lbm_adjoint_release": (i32, [vp]),
             "lbm_status": (i32, [vp]),
             "lbm_debug_persistent": (i32, [vp, i64, i64]),
+            "lbm_fd_create": (i32, [P(vp), i64, d, d, d, i32, P(lbm_phys), vp]),
+            "lbm_fd_destroy": (None, [vp]),
+            "lbm_fd_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_fd_steps_done": (i64, [vp]),
+            "lbm_fd_set_state": (i32, [vp, vp, vp, vp]),
+            "lbm_fd_set_fields": (i32, [vp, vp]),
+            "lbm_fd_step": (i32, [vp, i64]),
+            "lbm_fd_fields": (i32, [vp, vp, vp, vp]),
+            "lbm_fd_diagnostics": (i32, [vp, P(d), P(i32)]),
+            "lbm_fd_set_config": (i32, [vp, i32, i32, i32]),
+            "lbm_fd_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
+            "lbm_fd_autotune": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -373,3 +385,100 @@ class Lattice:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbm_steps_done(self.ctx))
+
+
+def _phys_struct(phys: dict | None):
+    if phys is None:
+        return None
+    base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, source_on=1, equilibria=0,
+                u0_lin=0.0, s0_lin=0.0)
+    base.update(phys)
+    return lbm_phys(**base)
+
+
+class FdGrid:
+    """Finite-difference comparison solver of section 9 (lbm_fd_* of the C-ABI): one periodic grid of
+    N >= 3 nodes, spacing dx, time step dt, kinematic viscosity nu; precision "f64" or "f32".
+    phys: dict of lbm_phys fields (gamma, Pr, cp, rho0, p0, s0, source_on); None = section 9 values."""
+
+    def __init__(self, N: int, dx: float, dt: float, nu: float, precision: str = "f64",
+                 phys: dict | None = None, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        install_torch_allocator()
+        ph = _phys_struct(phys)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.N = int(N)
+        ctx = ctypes.c_void_p()
+        rc = self.lib.lbm_fd_create(ctypes.byref(ctx), self.N, float(dx), float(dt), float(nu),
+                                    PRECISIONS[precision], None if ph is None else ctypes.byref(ph),
+                                    ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_fd_create failed")
+        self.ctx = ctx
+
+    def _check(self, rc: int, what: str):
+        if rc != LBM_OK:
+            raise LbmError(rc, f"{what}: {self.lib.lbm_fd_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm_fd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, rho, u, s):
+        a, b, c = (_Arr(x, self.N) for x in (rho, u, s))
+        self._check(self.lib.lbm_fd_set_state(self.ctx, a.ptr, b.ptr, c.ptr), "lbm_fd_set_state")
+
+    def set_fields(self, W):
+        """W: plane-major [3, N] (rho, J, zeta)."""
+        a = _Arr(W.reshape(-1) if hasattr(W, "reshape") else W, 3 * self.N)
+        self._check(self.lib.lbm_fd_set_fields(self.ctx, a.ptr), "lbm_fd_set_fields")
+
+    def step(self, nsteps: int):
+        self._check(self.lib.lbm_fd_step(self.ctx, int(nsteps)), "lbm_fd_step")
+
+    def fields(self, device: bool = False):
+        """(rho, J, zeta): torch tensors on the GPU (device=True) or numpy arrays."""
+        torch = _torch()
+        if device:
+            out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(3)]
+        else:
+            out = [np.empty(self.N) for _ in range(3)]
+        a = [_Arr(o, self.N, writable=True) for o in out]
+        self._check(self.lib.lbm_fd_fields(self.ctx, a[0].ptr, a[1].ptr, a[2].ptr), "lbm_fd_fields")
+        return out
+
+    def diagnostics(self):
+        """(sums [4] = (sum rho, sum J, sum zeta, sum rho E), flags, status)."""
+        sums = np.zeros(4)
+        flags = np.zeros(1, dtype=np.int32)
+        rc = self.lib.lbm_fd_diagnostics(self.ctx, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if rc not in (LBM_OK, LBM_ERR_UNSTABLE):
+            self._check(rc, "lbm_fd_diagnostics")
+        return sums, int(flags[0]), rc
+
+    def set_config(self, steps_per_launch: int = 0, block_threads: int = 0, nodes_per_thread: int = 0):
+        self._check(self.lib.lbm_fd_set_config(self.ctx, int(steps_per_launch), int(block_threads),
+                                               int(nodes_per_thread)), "lbm_fd_set_config")
+
+    def get_config(self):
+        k, nt, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm_fd_get_config(self.ctx, ctypes.byref(k), ctypes.byref(nt), ctypes.byref(v)),
+                    "lbm_fd_get_config")
+        return k.value, nt.value, v.value
+
+    def autotune(self, trials: int = 3):
+        self._check(self.lib.lbm_fd_autotune(self.ctx, int(trials)), "lbm_fd_autotune")
+        return self.get_config()
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbm_fd_steps_done(self.ctx))
