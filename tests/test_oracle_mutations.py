@@ -95,3 +95,41 @@ def test_fd_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_fd.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
+
+
+D1Q3_SRC = os.path.join(ROOT, "oracle", "d1q3_oracle.cpp")
+
+D1Q3_MUTANTS = {
+    "d1q3 e_eq pressure coefficient": ("eq[2] = 3.0 * (rho * u * u + pr) - 2.0 * p.lambda * p.lambda * rho;",
+                                       "eq[2] = 3.0 * (rho * u * u + 0.9 * pr) - 2.0 * p.lambda * p.lambda * rho;"),
+    "d1q3 e_eq kinetic term dropped": ("eq[2] = 3.0 * (rho * u * u + pr) - 2.0 * p.lambda * p.lambda * rho;",
+                                       "eq[2] = 3.0 * (pr) - 2.0 * p.lambda * p.lambda * rho;"),
+    "d1q3 e_eq lattice term": ("eq[2] = 3.0 * (rho * u * u + pr) - 2.0 * p.lambda * p.lambda * rho;",
+                               "eq[2] = 3.0 * (rho * u * u + pr) - 1.0 * p.lambda * p.lambda * rho;"),
+    "d1q3 EOS exponent": ("std::pow(rho / p.scale, p.gamma)", "std::pow(rho / p.scale, p.gamma - 1.0)"),
+    "d1q3 psi_eq sign": ("eq[1] = p.u0 * zeta;", "eq[1] = -p.u0 * zeta;"),
+    "d1q3 eps_eq drops a lambda": ("eq[2] = p.alpha * p.lambda * p.lambda * zeta;",
+                                   "eq[2] = p.alpha * p.lambda * zeta;"),
+    "d1q3 psi relaxed with s_eps": ("m[1] = m[1] + p.s_psi * (eq[1] - m[1]);", "m[1] = m[1] + p.s_eps * (eq[1] - m[1]);"),
+    "d1q3 e fully relaxed": ("m[2] = m[2] + p.s_e * (eq[2] - m[2]);", "m[2] = eq[2];"),
+    "d1q3 M energy row": ("{-2 * l * l, l * l, l * l}", "{-l * l, l * l, l * l}"),
+    "d1q3 M momentum row sign": ("{0, l, -l}", "{0, -l, l}"),
+    "d1q3 stream direction": ("f[3 * j + 1] = post[3 * l + 1];", "f[3 * j + 1] = post[3 * r + 1];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(D1Q3_MUTANTS))
+def test_d1q3_pins_catch_planted_mistake(name, tmp_path):
+    old, new = D1Q3_MUTANTS[name]
+    src = open(D1Q3_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not found exactly once"
+    mut = tmp_path / "d1q3_mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libd1q3_mutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-o", str(lib), str(mut)], check=True)
+    env = dict(os.environ, D1Q3_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_d1q3.py")],
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
