@@ -376,6 +376,74 @@ def run_fd(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
     return out
 
 
+# Single-distribution D1Q3 schemes (sections 2 and 4) on N = 2^26 nodes, lambda = 1: the fluid scheme
+# on the steepening wave (rho = 1 + 0.1 sin, J = rho 0.1 sin, s_e = 1.2, isentropic p0 (rho)^1.4) and
+# the advection-diffusion scheme on zeta = 1 + 0.1 sin (u0 = 0.1, alpha = 0, s_psi = 1.2, s_eps = 1.5).
+# Bytes per node per launch: three populations read and written.
+D1Q3_BYTES_PER_NODE = {"f32": 24, "f64": 48}
+# Arithmetic per computed node-step (halo included), keyed by (scheme, precision). FP64: executed
+# DFMA, DADD, DMUL from ncu at N = 2^23, (16, 256, 4), over 8457 x 1024 x 16 node-steps (CUDA's log1p,
+# expm1 and reciprocal included): fluid (2 x 5,819,498,496 + 1,662,713,856 + 1,524,154,368) / 138,559,488
+# = 107.0, advection-diffusion (2 x 831,356,928 + 831,356,928 + 554,237,952) / 138,559,488 = 22.0.
+# FP32 runs on paired lanes, which ncu's per-opcode counters do not split out; counted from the source
+# instead (fma = 2): fluid 66 (moments 5, 1/(1+r) 2, series log1p 22 and expm1 17, equilibrium and
+# relaxation 11, M^-1 9), advection-diffusion 22 (the FP64 count).
+D1Q3_FLOPS_PER_COMPUTED = {("fluid", "f64"): 14825865216 / 138559488, ("advection_diffusion", "f64"): 22.0,
+                           ("fluid", "f32"): 66.0, ("advection_diffusion", "f32"): 22.0}
+
+
+def run_d1q3(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
+    x = 2 * np.pi * np.arange(N) / N
+    rho = torch.from_numpy(1.0 + 0.1 * np.sin(x)).cuda()
+    J = rho * torch.from_numpy(0.1 * np.sin(x)).cuda()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    out = {}
+    for scheme in ("fluid", "advection_diffusion"):
+        out[scheme] = {}
+        for prec in args.precisions.split(","):
+            steps = args.d1q3_steps_f64 if prec == "f64" else args.d1q3_steps_f32
+            if scheme == "fluid":
+                lat = lbm.D1q3Lattice(N, "fluid", s_e=S_E, precision=prec)
+                state = (rho, J)
+            else:
+                lat = lbm.D1q3Lattice(N, "advection_diffusion", u0=0.1, alpha=0.0, s_psi=1.2, precision=prec)
+                state = (rho,)
+            lat.set_state(*state)
+            if args.d1q3_config:
+                lat.set_config(*[int(v) for v in args.d1q3_config.split(",")])
+                k, nt, v = lat.get_config()
+            else:
+                k, nt, v = lat.autotune(2)
+            lat.set_state(*state)
+            steps = max(k, (steps // k) * k)
+            ms = time_device(lat, torch, steps, 3 * k, None, 1)
+            _, flags, _ = lat.sums()
+            lat.close()
+            glups = N * steps / (ms * 1e-3) / 1e9
+            launch_ms = ms / (steps // k)
+            achieved = N * D1Q3_BYTES_PER_NODE[prec] / (launch_ms * 1e-3) / 1e9
+            r = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": k, "block_threads": nt,
+                 "nodes_per_thread": v, "launch_ms": launch_ms, "flags": int(flags),
+                 "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved / hbm_peak, "effective_gbs": glups * D1Q3_BYTES_PER_NODE[prec],
+                                  "effective_frac": glups * D1Q3_BYTES_PER_NODE[prec] / hbm_peak,
+                                  "algorithmic_bytes_per_launch": N * D1Q3_BYTES_PER_NODE[prec]}}
+            fl = D1Q3_FLOPS_PER_COMPUTED.get((scheme, prec))
+            if fl is not None:
+                fl = fl * nt * v / (nt * v - 2 * k)
+                a = glups * fl / 1e3
+                pk = props.multi_processor_count * FLOPS_PER_SM_CLOCK[prec] * sm_clock_mhz * 1e6 / 1e12
+                r["roofline"] = {"bound": "alu", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                                 "flops_per_node_update": fl,
+                                 "peak_kind": f"derived: {props.multi_processor_count} SMs x "
+                                              f"{FLOPS_PER_SM_CLOCK[prec]:.0f} {prec.upper()} flops/clock x "
+                                              f"{sm_clock_mhz:.0f} MHz"}
+            out[scheme][prec] = r
+    del rho, J
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank: int, world: int, local: int, dist):
     import torch
 
@@ -384,6 +452,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     torch.cuda.set_device(local)
     build.build()
     hbm_peak, peak_kind = measured_peaks()
+    if args.d1q3_only:
+        with ClockSampler(local) as clk:
+            res = run_d1q3(args, lbm, torch, args.nodes, hbm_peak, 2070.0)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "D1Q3 schemes", "nodes": args.nodes,
+                              "results": res, "clocks": clk.summary()}), flush=True)
+        return
     if args.fd_only:
         with ClockSampler(local) as clk:
             fd = run_fd(args, lbm, torch, args.nodes, hbm_peak, 2070.0)
@@ -453,6 +528,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     linear = None if args.no_linear else run_linear(args, lbm, torch)
     adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch)
     fdiff = None if args.no_fd else run_fd(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
+    d1q3 = None if args.no_d1q3 else run_d1q3(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
 
     if rank != 0:
         return
@@ -502,7 +578,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
                      "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
-            "finite_differences": fdiff,
+            "finite_differences": fdiff, "d1q3_schemes": d1q3,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
     print(json.dumps(line), flush=True)
@@ -531,6 +607,11 @@ def main():
     ap.add_argument("--fd-config", default="", help="k,block_threads,nodes_per_thread of the finite-difference kernel")
     ap.add_argument("--fd-steps-f64", type=int, default=200)
     ap.add_argument("--fd-steps-f32", type=int, default=1000)
+    ap.add_argument("--no-d1q3", action="store_true")
+    ap.add_argument("--d1q3-only", action="store_true", help="only the single-distribution D1Q3 leg at --nodes")
+    ap.add_argument("--d1q3-config", default="", help="k,block_threads,nodes_per_thread of the D1Q3 kernels")
+    ap.add_argument("--d1q3-steps-f64", type=int, default=500)
+    ap.add_argument("--d1q3-steps-f32", type=int, default=2000)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

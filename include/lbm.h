@@ -275,6 +275,74 @@ int lbm_fd_get_config(const lbm_fd_ctx *ctx, int32_t *steps_per_launch, int32_t 
  * launches per candidate. Synchronises. Needs a state. */
 int lbm_fd_autotune(lbm_fd_ctx *ctx, int32_t trials);
 
+/* ------------------------------------------------------------------------------------------------
+ * Single-distribution D1Q3 schemes (sections 2 and 4), the building blocks the coupled scheme is made
+ * of. One periodic lattice of N nodes, dx = 1, dt = 1/lambda, three populations (f0, f+, f-) with the
+ * moments of eq. (M-d1q3), m = scale (sum f, lambda (f+ - f-), lambda^2 (f+ + f- - 2 f0)).
+ *  LBM_D1Q3_FLUID (section 2): m = (rho, J, e); rho, J conserved; e relaxed with s_e toward
+ *    e_eq = 3 (rho u^2 + p) - 2 lambda^2 rho (eq. energie-equilibre), with the isentropic pressure
+ *    p = p0 (rho / rho0)^gamma (rho0 = scale). The paper names the isentropic Navier-Stokes equations
+ *    but no pressure law; this polytropic one is eq. (gaz-parfait) at s = s0.
+ *  LBM_D1Q3_ADVECTION_DIFFUSION (section 4): m = (zeta, psi, eps); zeta conserved; psi relaxed with
+ *    s_psi toward psi_eq = u0 zeta, eps with s_eps toward eps_eq = alpha lambda^2 zeta. Section 4
+ *    identifies the diffusivity: ((2 + alpha)/3 lambda^2 - u0^2)(1/s_psi - 1/2) dt = kappa; it states
+ *    stability for -2 < alpha < 1.
+ * Then f* = M^{-1} m* and advection: f0 stays, f+ moves to x + dx, f- to x - dx.
+ * Same status codes, pointer and stream conventions as the coupled scheme. */
+enum { LBM_D1Q3_FLUID = 0, LBM_D1Q3_ADVECTION_DIFFUSION = 1 };
+
+typedef struct {
+  int32_t scheme; /* LBM_D1Q3_FLUID or LBM_D1Q3_ADVECTION_DIFFUSION */
+  int32_t pad;
+  double lambda;  /* > 0 */
+  double scale;   /* rho0 (fluid) or zeta0 (advection-diffusion) of eq. (M-d1q3); <= 0 selects 1 */
+  double s_e;     /* fluid: relaxation rate of e, in (0, 2) */
+  double gamma;   /* fluid: isentropic exponent >= 1; <= 0 selects 1.4 */
+  double p0;      /* fluid: pressure at rho0; <= 0 selects rho0 c0^2 / gamma with c0 = lambda / 2 */
+  double u0;      /* advection-diffusion: advection velocity */
+  double alpha;   /* advection-diffusion: eps_eq = alpha lambda^2 zeta */
+  double kappa;   /* advection-diffusion: diffusivity, used when s_psi <= 0 (identification above) */
+  double s_psi;   /* advection-diffusion: rate of psi in (0, 2); <= 0: from kappa */
+  double s_eps;   /* advection-diffusion: rate of eps in (0, 2); <= 0 selects 1.5 (section 4) */
+} lbm_d1q3_params;
+
+typedef struct lbm_d1q3_ctx lbm_d1q3_ctx;
+
+/* N >= 3 periodic nodes; precision LBM_F64 or LBM_F32_SHIFTED (FP32 populations shifted by those of
+ * the rest state rho0, J = 0 or zeta0). LBM_ERR_INVALID_ARG for a rate outside (0, 2), lambda <= 0,
+ * or a kappa that no s_psi in (0, 2) reproduces. */
+int lbm_d1q3_create(lbm_d1q3_ctx **out, int64_t N, const lbm_d1q3_params *params, int32_t precision,
+                    void *stream);
+void lbm_d1q3_destroy(lbm_d1q3_ctx *ctx);
+const char *lbm_d1q3_last_error(const lbm_d1q3_ctx *ctx);
+int64_t lbm_d1q3_steps_done(const lbm_d1q3_ctx *ctx);
+/* The rates in use: fluid (s_e, 0); advection-diffusion (s_psi, s_eps). Host outputs, may be NULL. */
+int lbm_d1q3_rates(const lbm_d1q3_ctx *ctx, double *s1, double *s2);
+/* Equilibrium state from per-node conserved moments (N float64, host or device): fluid m0 = rho,
+ * m1 = J; advection-diffusion m0 = zeta (m1 unused, may be NULL). Resets the step counter. */
+int lbm_d1q3_set_state(lbm_d1q3_ctx *ctx, const double *m0, const double *m1);
+/* Advances nsteps >= 0 time steps (enqueued; no synchronisation). */
+int lbm_d1q3_step(lbm_d1q3_ctx *ctx, int64_t nsteps);
+/* Moments m = M f per node: (rho, J, e) or (zeta, psi, eps), N float64 each, host or device, any NULL. */
+int lbm_d1q3_moments(lbm_d1q3_ctx *ctx, double *m0, double *m1, double *m2);
+/* Populations (f0, f+, f-) as float64, plane-major [3][N], host or device (shift removed / applied). */
+int lbm_d1q3_get_populations(lbm_d1q3_ctx *ctx, double *f);
+int lbm_d1q3_set_populations(lbm_d1q3_ctx *ctx, const double *f);
+/* FP64 sums of the three moments over the lattice in a fixed order (host sums[3]) and flag bits
+ * (host flags[1]: bit 0 non-finite population, bit 1 rho <= 0 for the fluid scheme); synchronises;
+ * LBM_ERR_UNSTABLE if a flag is set (outputs still filled). */
+int lbm_d1q3_sums(lbm_d1q3_ctx *ctx, double *sums, int32_t *flags);
+/* Kernel configuration: steps_per_launch k in 1..64 (k halo nodes per tile side), block_threads in
+ * {128, 256, 512}, nodes_per_thread in {1, 2, 4, 8}, block_threads * nodes_per_thread - 2k >= 32;
+ * 0 keeps the current value. Default 8, 256, 4. */
+int lbm_d1q3_set_config(lbm_d1q3_ctx *ctx, int32_t steps_per_launch, int32_t block_threads,
+                        int32_t nodes_per_thread);
+int lbm_d1q3_get_config(const lbm_d1q3_ctx *ctx, int32_t *steps_per_launch, int32_t *block_threads,
+                        int32_t *nodes_per_thread);
+/* Times every valid configuration on the current state (left unchanged; trials write only the spare
+ * buffer, over at most 16384 tiles) and keeps the fastest per node-update. Synchronises. */
+int lbm_d1q3_autotune(lbm_d1q3_ctx *ctx, int32_t trials);
+
 #ifdef __cplusplus
 }
 #endif

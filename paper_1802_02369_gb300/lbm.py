@@ -57,6 +57,18 @@ class lbm_phys(ctypes.Structure):
                 ("u0_lin", ctypes.c_double), ("s0_lin", ctypes.c_double)]
 
 
+LBM_D1Q3_FLUID = 0
+LBM_D1Q3_ADVECTION_DIFFUSION = 1
+D1Q3_SCHEMES = {"fluid": LBM_D1Q3_FLUID, "advection_diffusion": LBM_D1Q3_ADVECTION_DIFFUSION}
+
+
+class lbm_d1q3_params(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("pad", ctypes.c_int32), ("lam", ctypes.c_double),
+                ("scale", ctypes.c_double), ("s_e", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("p0", ctypes.c_double), ("u0", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("s_psi", ctypes.c_double), ("s_eps", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -124,6 +136,20 @@ def load_library(path: str = LIB_PATH):
             "lbm_fd_set_config": (i32, [vp, i32, i32, i32]),
             "lbm_fd_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
             "lbm_fd_autotune": (i32, [vp, i32]),
+            "lbm_d1q3_create": (i32, [P(vp), i64, P(lbm_d1q3_params), i32, vp]),
+            "lbm_d1q3_destroy": (None, [vp]),
+            "lbm_d1q3_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_d1q3_steps_done": (i64, [vp]),
+            "lbm_d1q3_rates": (i32, [vp, P(d), P(d)]),
+            "lbm_d1q3_set_state": (i32, [vp, vp, vp]),
+            "lbm_d1q3_step": (i32, [vp, i64]),
+            "lbm_d1q3_moments": (i32, [vp, vp, vp, vp]),
+            "lbm_d1q3_get_populations": (i32, [vp, vp]),
+            "lbm_d1q3_set_populations": (i32, [vp, vp]),
+            "lbm_d1q3_sums": (i32, [vp, P(d), P(i32)]),
+            "lbm_d1q3_set_config": (i32, [vp, i32, i32, i32]),
+            "lbm_d1q3_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
+            "lbm_d1q3_autotune": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -482,3 +508,106 @@ class FdGrid:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbm_fd_steps_done(self.ctx))
+
+
+class D1q3Lattice:
+    """Single-distribution D1Q3 scheme of section 2 (scheme="fluid": s_e, gamma, p0, scale = rho0) or
+    section 4 (scheme="advection_diffusion": u0, alpha, kappa or s_psi, s_eps, scale = zeta0) on one
+    periodic lattice of N >= 3 nodes (lbm_d1q3_* of the C-ABI); precision "f64" or "f32"."""
+
+    def __init__(self, N: int, scheme: str = "fluid", lam: float = 1.0, precision: str = "f64", stream=None,
+                 **params):
+        torch = _torch()
+        self.lib = load_library()
+        install_torch_allocator()
+        base = dict(scheme=D1Q3_SCHEMES[scheme], pad=0, lam=lam, scale=0.0, s_e=1.5, gamma=0.0, p0=0.0, u0=0.0,
+                    alpha=0.0, kappa=0.0, s_psi=0.0, s_eps=0.0)
+        unknown = set(params) - set(base)
+        if unknown:
+            raise TypeError(f"unknown D1Q3 parameters {sorted(unknown)}")
+        base.update(params)
+        self.params = lbm_d1q3_params(**base)
+        self.scheme = scheme
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.N = int(N)
+        ctx = ctypes.c_void_p()
+        rc = self.lib.lbm_d1q3_create(ctypes.byref(ctx), self.N, ctypes.byref(self.params), PRECISIONS[precision],
+                                      ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_d1q3_create failed")
+        self.ctx = ctx
+
+    def _check(self, rc: int, what: str):
+        if rc != LBM_OK:
+            raise LbmError(rc, f"{what}: {self.lib.lbm_d1q3_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm_d1q3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.lbm_d1q3_rates(self.ctx, ctypes.byref(a), ctypes.byref(b)), "lbm_d1q3_rates")
+        return a.value, b.value
+
+    def set_state(self, m0, m1=None):
+        a = _Arr(m0, self.N)
+        b = None if m1 is None else _Arr(m1, self.N)
+        self._check(self.lib.lbm_d1q3_set_state(self.ctx, a.ptr, None if b is None else b.ptr), "lbm_d1q3_set_state")
+
+    def step(self, nsteps: int):
+        self._check(self.lib.lbm_d1q3_step(self.ctx, int(nsteps)), "lbm_d1q3_step")
+
+    def moments(self, device: bool = False):
+        torch = _torch()
+        if device:
+            out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(3)]
+        else:
+            out = [np.empty(self.N) for _ in range(3)]
+        a = [_Arr(o, self.N, writable=True) for o in out]
+        self._check(self.lib.lbm_d1q3_moments(self.ctx, a[0].ptr, a[1].ptr, a[2].ptr), "lbm_d1q3_moments")
+        return out
+
+    def populations(self):
+        out = np.empty(3 * self.N)
+        self._check(self.lib.lbm_d1q3_get_populations(self.ctx, out.ctypes.data), "lbm_d1q3_get_populations")
+        return out.reshape(3, self.N)
+
+    def set_populations(self, f):
+        a = _Arr(f.reshape(-1) if hasattr(f, "reshape") else f, 3 * self.N)
+        self._check(self.lib.lbm_d1q3_set_populations(self.ctx, a.ptr), "lbm_d1q3_set_populations")
+
+    def sums(self):
+        """(sums [3] of the three moments, flags, status)."""
+        sums = np.zeros(3)
+        flags = np.zeros(1, dtype=np.int32)
+        rc = self.lib.lbm_d1q3_sums(self.ctx, sums.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if rc not in (LBM_OK, LBM_ERR_UNSTABLE):
+            self._check(rc, "lbm_d1q3_sums")
+        return sums, int(flags[0]), rc
+
+    def set_config(self, steps_per_launch: int = 0, block_threads: int = 0, nodes_per_thread: int = 0):
+        self._check(self.lib.lbm_d1q3_set_config(self.ctx, int(steps_per_launch), int(block_threads),
+                                                 int(nodes_per_thread)), "lbm_d1q3_set_config")
+
+    def get_config(self):
+        k, nt, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm_d1q3_get_config(self.ctx, ctypes.byref(k), ctypes.byref(nt), ctypes.byref(v)),
+                    "lbm_d1q3_get_config")
+        return k.value, nt.value, v.value
+
+    def autotune(self, trials: int = 3):
+        self._check(self.lib.lbm_d1q3_autotune(self.ctx, int(trials)), "lbm_d1q3_autotune")
+        return self.get_config()
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbm_d1q3_steps_done(self.ctx))
