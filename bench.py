@@ -286,9 +286,11 @@ def run_adjoint(args, lbm, torch):
     differentiated run per second, over forward + backward."""
     from paper_1802_02369_gb300 import workloads as W
 
-    B, N = 256, 65536
+    B, N = args.adjoint_lattices, 65536
     out = {}
     for prec, T in (("f32", args.adjoint_steps_f32), ("f64", args.adjoint_steps_f64)):
+        if prec not in args.precisions.split(","):
+            continue
         rho, u, p = W.gaussian_bumps(B, N, 2369, W.reference_pressure())
         rho_t, u_t, p_t = W.gaussian_bumps(B, N, 2370, W.reference_pressure())
         tgt_lat = lbm.Lattice(np.full(B, N), s_e=1.5, precision=prec)
@@ -297,6 +299,7 @@ def run_adjoint(args, lbm, torch):
         target = tgt_lat.moments(device=True)[0]
         tgt_lat.close()
         lat = lbm.Lattice(np.full(B, N), s_e=1.5, precision=prec)
+        adj_k = lat.get_adjoint_config()
         d = [torch.from_numpy(x.ravel()).cuda() for x in (rho, u, p)]
         lat.set_state(*d)
         torch.cuda.synchronize()
@@ -313,6 +316,7 @@ def run_adjoint(args, lbm, torch):
         torch.cuda.empty_cache()
         out[prec] = {"value": B * N * T / dt / 1e9, "unit": "GLUPS (differentiated node-steps / s)", "T": T,
                      "lattices": B, "N": N, "seconds": dt, "checkpoint_segment": int(round(T ** 0.5)),
+                     "reverse_steps_per_launch": adj_k,
                      "dL_dse_first_lattice": float(g_rates[0, 0])}
     return out
 
@@ -452,6 +456,11 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     torch.cuda.set_device(local)
     build.build()
     hbm_peak, peak_kind = measured_peaks()
+    if args.adjoint_only:
+        res = run_adjoint(args, lbm, torch)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "adjoint", "results": res}), flush=True)
+        return
     if args.d1q3_only:
         with ClockSampler(local) as clk:
             res = run_d1q3(args, lbm, torch, args.nodes, hbm_peak, 2070.0)
@@ -607,6 +616,8 @@ def main():
     ap.add_argument("--fd-config", default="", help="k,block_threads,nodes_per_thread of the finite-difference kernel")
     ap.add_argument("--fd-steps-f64", type=int, default=200)
     ap.add_argument("--fd-steps-f32", type=int, default=1000)
+    ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint leg")
+    ap.add_argument("--adjoint-lattices", type=int, default=256)
     ap.add_argument("--no-d1q3", action="store_true")
     ap.add_argument("--d1q3-only", action="store_true", help="only the single-distribution D1Q3 leg at --nodes")
     ap.add_argument("--d1q3-config", default="", help="k,block_threads,nodes_per_thread of the D1Q3 kernels")

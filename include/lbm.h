@@ -205,6 +205,16 @@ int lbm_adjoint_backward(lbm_ctx *ctx, const double *dL_drho_T, double *dL_drho0
 int lbm_adjoint(lbm_ctx *ctx, int64_t T, const double *rho_target, double *loss, double *dL_drho0,
                 double *dL_du0, double *dL_drates);
 int lbm_adjoint_release(lbm_ctx *ctx);
+/* Reverse steps per launch of the backward sweep: 1, 2, 4 or 8 (0 selects the default: 4 for
+ * LBM_F32_SHIFTED, where it halves the backward time against 1, and 1 for LBM_F64, whose arithmetic
+ * bound makes the on-chip recomputation of inner states a net cost). Each
+ * segment is split into blocks of that many steps; the states at the block starts are recomputed
+ * with launches of the step kernel, and one launch per block recomputes the block's inner states on
+ * chip and runs its reverse steps (HBM traffic per node-step falls with the depth; the tile halo,
+ * 4k - 2 nodes per side of 256, grows with it). The gradients do not depend on it beyond rounding
+ * (FP64: the forward recomputation is bitwise that of the step kernel). */
+int lbm_adjoint_set_config(lbm_ctx *ctx, int32_t steps_per_launch);
+int lbm_adjoint_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch);
 
 /* Diagnostics that allocate no device memory. The paper has no counterpart: this exists for callers
  * that cannot call cudaMalloc (code inside host callbacks or another framework's memory pool, or a

@@ -405,9 +405,10 @@ struct lbm_ctx {
   long long adj_T = -1, adj_seg = 0, adj_nseg = 0;
   std::vector<void*> ckpt, stash;
   void* adj_a[2] = {nullptr, nullptr};
-  LatDev* d_lat_adj = nullptr;
-  long long adj_ntiles = 0;
-  double* d_gtile = nullptr;
+  int adj_K = 4;                    // reverse steps per adjoint launch (lbm_adjoint_set_config)
+  LatDev* d_lat_adj = nullptr;      // per depth K = 1 .. kAdjointMaxK: B records with the adjoint tiling
+  long long adj_ntiles[lbm::kAdjointMaxK] = {};
+  double* d_gtile[lbm::kAdjointMaxK] = {};
   double* d_rgrad = nullptr;
   double* d_lpart = nullptr;
   double* d_loss = nullptr;
@@ -601,6 +602,7 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   c->offset[B] = tot;
   c->Ntot = tot;
   c->K = (precision == LBM_F64) ? 1 : 4;
+  c->adj_K = (precision == LBM_F64) ? 1 : 4;  // measured fastest (FP64 is bound by its arithmetic)
   c->NT = (precision == LBM_F64) ? 512 : 256;
   c->V = (precision == LBM_F64) ? 1 : 2;
   rebuild_tables(c);
@@ -779,7 +781,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   lbm_adjoint_release(c);
   dev_free(c->d_lat_adj);
-  dev_free(c->d_gtile);
+  for (double* g : c->d_gtile) dev_free(g);
   dev_free(c->d_rgrad);
   dev_free(c->d_lpart);
   dev_free(c->d_loss);
@@ -1035,22 +1037,27 @@ namespace {
 
 int adjoint_setup(lbm_ctx* c) {
   if (c->d_lat_adj) return LBM_OK;
-  std::vector<LatDev> tab(c->host_lat);
-  const long long bout = lbm::kAdjointThreads - 4;
-  long long t = 0;
-  for (int b = 0; b < c->B; ++b) {
-    tab[b].tile0 = t;
-    t += (c->N[b] + bout - 1) / bout;
+  // Tile tables of the adjoint for every depth K (tiles store adjoint_tile_out(K) nodes).
+  std::vector<LatDev> tab((size_t)lbm::kAdjointMaxK * c->B);
+  for (int K = 1; K <= lbm::kAdjointMaxK; ++K) {
+    const long long bout = lbm::adjoint_tile_out(K);
+    long long t = 0;
+    for (int b = 0; b < c->B; ++b) {
+      LatDev d = c->host_lat[b];
+      d.tile0 = t;
+      tab[(size_t)(K - 1) * c->B + b] = d;
+      t += (c->N[b] + bout - 1) / bout;
+    }
+    c->adj_ntiles[K - 1] = t;
+    if (!c->d_gtile[K - 1]) c->d_gtile[K - 1] = (double*)dev_alloc(sizeof(double) * 2 * t, c->stream);
+    if (!c->d_gtile[K - 1]) return fail(c, LBM_ERR_OOM, "adjoint: allocation failed");
   }
-  c->adj_ntiles = t;
-  c->d_lat_adj = (LatDev*)dev_alloc(sizeof(LatDev) * c->B, c->stream);
-  c->d_gtile = (double*)dev_alloc(sizeof(double) * 2 * t, c->stream);
-  c->d_rgrad = (double*)dev_alloc(sizeof(double) * 2 * c->B, c->stream);
-  c->d_lpart = (double*)dev_alloc(sizeof(double) * ((c->Ntot + 255) / 256), c->stream);
-  c->d_loss = (double*)dev_alloc(sizeof(double), c->stream);
-  if (!c->d_lat_adj || !c->d_gtile || !c->d_rgrad || !c->d_lpart || !c->d_loss)
-    return fail(c, LBM_ERR_OOM, "adjoint: allocation failed");
-  LBM_CK(c, cudaMemcpyAsync(c->d_lat_adj, tab.data(), sizeof(LatDev) * c->B, cudaMemcpyHostToDevice, c->stream));
+  if (!c->d_rgrad) c->d_rgrad = (double*)dev_alloc(sizeof(double) * 2 * c->B, c->stream);
+  if (!c->d_lpart) c->d_lpart = (double*)dev_alloc(sizeof(double) * ((c->Ntot + 255) / 256), c->stream);
+  if (!c->d_loss) c->d_loss = (double*)dev_alloc(sizeof(double), c->stream);
+  c->d_lat_adj = (LatDev*)dev_alloc(sizeof(LatDev) * tab.size(), c->stream);
+  if (!c->d_lat_adj || !c->d_rgrad || !c->d_lpart || !c->d_loss) return fail(c, LBM_ERR_OOM, "adjoint: allocation failed");
+  LBM_CK(c, cudaMemcpyAsync(c->d_lat_adj, tab.data(), sizeof(LatDev) * tab.size(), cudaMemcpyHostToDevice, c->stream));
   LBM_CK(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -1093,27 +1100,34 @@ int adjoint_forward_impl(lbm_ctx* c, long long T) {
   return LBM_OK;
 }
 
-// Reverse sweep from the seed already in adj_a[0]; leaves dL/df(0) in adj_a[res].
+// Reverse sweep from the seed already in adj_a[0]; leaves dL/df(0) in adj_a[res]. Each segment of
+// sqrt(T) steps is split into blocks of adj_K steps: the states at the block starts are recomputed
+// from the segment's checkpoint with adj_K-step launches of the step kernel, then every block runs its
+// reverse steps in one launch (which recomputes the block's inner states on chip).
 template <typename R>
 int adjoint_reverse(lbm_ctx* c, int* res) {
   const lbm::ConstSet<R> k = make_constset<R>(c->ph);
-  LBM_CK(c, cudaMemsetAsync(c->d_gtile, 0, sizeof(double) * 2 * c->adj_ntiles, c->stream));
+  const int KA = c->adj_K;
+  for (int K = 1; K <= lbm::kAdjointMaxK; ++K)
+    LBM_CK(c, cudaMemsetAsync(c->d_gtile[K - 1], 0, sizeof(double) * 2 * c->adj_ntiles[K - 1], c->stream));
   int a = 0;
   for (long long j = c->adj_nseg - 1; j >= 0; --j) {
     const long long len = std::min(c->adj_seg, c->adj_T - j * c->adj_seg);
-    // States t0 .. t0 + len - 1 of this segment: the checkpoint, then recomputed one step at a time.
-    std::vector<const R*> st(len);
+    const long long nb = (len + KA - 1) / KA;
+    std::vector<const R*> st(nb);
     st[0] = (const R*)c->ckpt[j];
-    for (long long i = 1; i < len; ++i) {
-      cudaError_t e = lbm::launch_step_tiles<R>(st[i - 1], (R*)c->stash[i - 1], c->Ntot, lat_for(c, 1),
-                                                tile_map_for(c, 1), c->B, c->ntiles_k[0], 1, c->NT, c->V, k, c->stream,
-                                                0);
+    for (long long b = 1; b < nb; ++b) {
+      cudaError_t e = lbm::launch_step_tiles<R>(st[b - 1], (R*)c->stash[b - 1], c->Ntot, lat_for(c, KA),
+                                                tile_map_for(c, KA), c->B, c->ntiles_k[depth_index(KA)], KA, c->NT,
+                                                c->V, k, c->stream, 0);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint recompute");
-      st[i] = (const R*)c->stash[i - 1];
+      st[b] = (const R*)c->stash[b - 1];
     }
-    for (long long i = len - 1; i >= 0; --i) {
-      cudaError_t e = lbm::launch_adjoint_step<R>(st[i], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot,
-                                                  c->d_lat_adj, c->B, c->adj_ntiles, k.s, c->d_gtile, c->stream);
+    for (long long b = nb - 1; b >= 0; --b) {
+      const int Kb = (int)std::min<long long>(KA, len - b * KA);
+      cudaError_t e = lbm::launch_adjoint_block<R>(st[b], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot,
+                                                   c->d_lat_adj + (size_t)(Kb - 1) * c->B, c->B,
+                                                   c->adj_ntiles[Kb - 1], Kb, k.s, c->d_gtile[Kb - 1], c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
       a = 1 - a;
     }
@@ -1149,7 +1163,9 @@ int adjoint_backward_impl(lbm_ctx* c, const double* target, const double* rho_b,
   e = lbm::launch_adjoint_init<R>((const R*)c->ckpt[0], (const R*)c->adj_a[a], n, c->d_lat, c->B,
                                   make_consts<double>(c->ph), d_drho, d_du, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint init");
-  e = lbm::launch_reduce_rate_grads(c->d_gtile, c->d_lat_adj, c->B, c->adj_ntiles, c->d_rgrad, c->stream);
+  for (int K = 1; K <= lbm::kAdjointMaxK && e == cudaSuccess; ++K)  // fixed order over the depths
+    e = lbm::launch_reduce_rate_grads(c->d_gtile[K - 1], c->d_lat_adj + (size_t)(K - 1) * c->B, c->B,
+                                      c->adj_ntiles[K - 1], c->d_rgrad, K > 1, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint rate reduction");
   if (dfd0) {
     // dL/df(0) as float64 (the population shift is a constant and does not change the gradient).
@@ -1209,6 +1225,21 @@ int lbm_adjoint_release(lbm_ctx* c) {
   c->stash.clear();
   for (int k = 0; k < 2; ++k) { dev_free(c->adj_a[k]); c->adj_a[k] = nullptr; }
   c->adj_T = -1;
+  return LBM_OK;
+}
+
+int lbm_adjoint_set_config(lbm_ctx* c, int32_t steps_per_launch) {
+  if (!c) return LBM_ERR_INVALID_ARG;
+  const int K = steps_per_launch > 0 ? steps_per_launch : (c->precision == LBM_F64 ? 1 : 4);
+  if (K != 1 && K != 2 && K != 4 && K != 8)
+    return fail(c, LBM_ERR_INVALID_ARG, "adjoint_set_config: steps_per_launch must be 1, 2, 4 or 8");
+  c->adj_K = K;
+  return LBM_OK;
+}
+
+int lbm_adjoint_get_config(const lbm_ctx* c, int32_t* steps_per_launch) {
+  if (!c || !steps_per_launch) return LBM_ERR_INVALID_ARG;
+  *steps_per_launch = c->adj_K;
   return LBM_OK;
 }
 

@@ -367,13 +367,16 @@ cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* l
                               long long ntiles, int K, int NT, int V, long long nblocks, const PersistentCtl& ctl,
                               const ConstSet<R>& c, cudaStream_t st);
 
-// Adjoint (lbm_adjoint.cu): one step per launch, tiles of kAdjointThreads nodes (halo 2 per side).
+// Adjoint (lbm_adjoint.cu): K <= kAdjointMaxK reverse steps per launch from the forward state at the
+// start of the block, tiles of kAdjointThreads nodes storing kAdjointThreads - 2(4K - 2) of them.
 constexpr int kAdjointThreads = 256;
+constexpr int kAdjointMaxK = 8;
+inline int adjoint_tile_out(int K) { return kAdjointThreads - 2 * (4 * K - 2); }
 template <typename R>
-cudaError_t launch_adjoint_step(const R* fin, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
-                                long long ntiles, const Consts<R>& c, double* grad_tile, cudaStream_t st);
+cudaError_t launch_adjoint_block(const R* f0, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
+                                 long long ntiles, int K, const Consts<R>& c, double* grad_tile, cudaStream_t st);
 cudaError_t launch_reduce_rate_grads(const double* grad_tile, const LatDev* lat, int B, long long ntiles, double* out,
-                                     cudaStream_t st);
+                                     bool accumulate, cudaStream_t st);
 template <typename R>
 cudaError_t launch_adjoint_init(const R* f0, const R* a0, long long plane, const LatDev* lat, int B,
                                 const Consts<double>& c, double* drho, double* du, cudaStream_t st);

@@ -122,6 +122,8 @@ def load_library(path: str = LIB_PATH):
             "lbm_adjoint_backward": (i32, [vp, vp, vp, vp, vp, vp]),
             "lbm_adjoint": (i32, [vp, i64, vp, vp, vp, vp, vp]),
             "lbm_adjoint_release": (i32, [vp]),
+            "lbm_adjoint_set_config": (i32, [vp, i32]),
+            "lbm_adjoint_get_config": (i32, [vp, P(i32)]),
             "lbm_status": (i32, [vp]),
             "lbm_debug_persistent": (i32, [vp, i64, i64]),
             "lbm_fd_create": (i32, [P(vp), i64, d, d, d, i32, P(lbm_phys), vp]),
@@ -385,6 +387,15 @@ class Lattice:
 
     def adjoint_release(self):
         self._check(self.lib.lbm_adjoint_release(self.ctx), "lbm_adjoint_release")
+
+    def set_adjoint_config(self, steps_per_launch: int = 0):
+        """Reverse steps per launch of the backward sweep (1, 2, 4, 8; 0 = the default: 4 in FP32, 1 in FP64)."""
+        self._check(self.lib.lbm_adjoint_set_config(self.ctx, int(steps_per_launch)), "lbm_adjoint_set_config")
+
+    def get_adjoint_config(self) -> int:
+        k = ctypes.c_int32()
+        self._check(self.lib.lbm_adjoint_get_config(self.ctx, ctypes.byref(k)), "lbm_adjoint_get_config")
+        return k.value
 
     def set_mode(self, mode: str):
         """"launch" (one kernel per k steps), "persistent" or "graph" (persistent, CUDA graph)."""

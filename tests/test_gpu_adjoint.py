@@ -252,3 +252,30 @@ def test_adjoint_full_batch_consistency_and_probes(lbm):
         fdiff = (L(r0 + h * vr, u0 + h * vu) - L(r0 - h * vr, u0 - h * vu)) / (2 * h)
         grad = np.dot(g_rho, vr) + np.dot(g_u, vu)
         assert abs(grad - fdiff) <= 1e-6 * abs(grad), (grad, fdiff)
+
+
+@pytest.mark.parametrize("T", [37, 50, 64])
+def test_adjoint_depths_agree(lbm, T):
+    """The backward sweep gives the same gradients for 1, 2, 4 or 8 reverse steps per launch. In FP64
+    the forward recomputation on chip is bitwise that of the step kernel, so dL/drho0 and dL/du0 are
+    bitwise equal and only the summation order of the rate gradients differs. The segment lengths
+    round(sqrt(T)) = 6, 7, 8 leave blocks of every length from 1 to 8."""
+    lengths, bc, s_e, data, targets = _case()
+    init = [np.concatenate([d[k] for d in data]) for k in range(3)]
+    res = {}
+    for prec in ("f64", "f32"):
+        for K in (1, 2, 4, 8):
+            lat = lbm.Lattice(lengths, s_e=s_e, bc=bc, precision=prec)
+            lat.set_adjoint_config(K)
+            assert lat.get_adjoint_config() == K
+            lat.set_state_entropy(*init)
+            res[prec, K] = lat.adjoint(T, np.concatenate(targets))
+            lat.close()
+    for K in (2, 4, 8):
+        a, b = res["f64", K], res["f64", 1]
+        assert a[0] == b[0]
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        assert np.abs(a[3] - b[3]).max() <= 1e-13 * np.abs(b[3]).max()
+        for i in (1, 2, 3):  # FP32: the inner states are recomputed in scalar lanes
+            c, d = res["f32", K][i], res["f64", 1][i]
+            assert np.abs(c - d).max() <= 2e-4 * np.abs(d).max(), (K, i)
