@@ -14,160 +14,268 @@
 
 namespace lbm {
 
-// Shared-memory exchange buffers of one CTA of NT threads (one node per thread).
-template <typename R, int NT>
+// Lanes: a thread holds W consecutive nodes in one lane value X (W = 1: X = double or float; W = 2:
+// X = float2, two nodes on Blackwell's paired FP32 instructions).
+template <typename X>
+struct Lane {
+  using R = X;
+  static constexpr int W = 1;
+};
+template <>
+struct Lane<float2> {
+  using R = float;
+  static constexpr int W = 2;
+};
+__device__ __forceinline__ double lget(double x, int) { return x; }
+__device__ __forceinline__ float lget(float x, int) { return x; }
+__device__ __forceinline__ float lget(float2 x, int j) { return j ? x.y : x.x; }
+__device__ __forceinline__ void lset(double& x, int, double v) { x = v; }
+__device__ __forceinline__ void lset(float& x, int, float v) { x = v; }
+__device__ __forceinline__ void lset(float2& x, int j, float v) {
+  if (j) x.y = v;
+  else x.x = v;
+}
+template <typename X>
+__device__ __forceinline__ X lit(double v) {
+  if constexpr (Lane<X>::W == 2) return make_float2((float)v, (float)v);
+  else return X(v);
+}
+template <typename X>
+__device__ __forceinline__ X lit_r(typename Lane<X>::R v) {
+  if constexpr (Lane<X>::W == 2) return make_float2(v, v);
+  else return v;
+}
+// Per-lane select: lane j takes a where b[j], else keeps x.
+template <typename X>
+__device__ __forceinline__ X sel(const bool (&b)[Lane<X>::W], X a, X x) {
+#pragma unroll
+  for (int j = 0; j < Lane<X>::W; ++j)
+    if (b[j]) lset(x, j, lget(a, j));
+  return x;
+}
+
+// Shared-memory exchange buffers of one CTA of NT threads, one lane value per thread (W nodes), so a
+// thread's accesses are single 4- or 8-byte words (no bank conflicts).
+template <typename X, int NT>
 struct AdjShared {
-  R su[NT], sT[NT];                 // forward u and T (or u' and theta in the recompute) of each node
-  R sap[NT][2], sam[NT][2];         // a+ and a- (f, g) of each node at t + 1; moving populations forward
-  R sul[NT], sur[NT], sTl[NT], sTr[NT];  // source adjoints scattered to the neighbours
+  X su[NT], sT[NT];                      // forward u and T (u' and theta in the recomputation)
+  X sfp[NT], sgp[NT], sfm[NT], sgm[NT];  // a+ (f, g) and a- (f, g) at t + 1; moving populations forward
+  X sul[NT], sur[NT], sTl[NT], sTr[NT];  // source adjoints scattered to the neighbours
   double sg[2][NT / 32];
 };
 
-// One adjoint step of node n (all threads of the CTA call it together; two CTA barriers): from the
-// forward state f = f(t) and a = a(t+1) of this node to ao = a(t) and this node's terms of dL/ds_e and
-// dL/ds_psi. Valid where f and a are valid two nodes to each side.
-template <typename R, int NT>
-__device__ __forceinline__ void adjoint_node_step(const R (&f)[6], const R (&a)[6], AdjShared<R, NT>& sh, int n,
-                                                  bool lw, bool rw, bool active, R s_e, R s_psi, R s_eps, R q, R s0,
-                                                  const Consts<R>& c, R (&ao)[6], R& g_se, R& g_sp) {
-  // Phase 1: forward state of this node, its adjoint at t + 1.
-  Node<R> m;
-  node_state(f, c, s0, m);
-  sh.su[n] = m.u;
-  sh.sT[n] = m.T;
-  sh.sap[n][0] = a[1]; sh.sap[n][1] = a[4];
-  sh.sam[n][0] = a[2]; sh.sam[n][1] = a[5];
+// Per-node flags of a thread's W nodes.
+template <int W>
+struct NodeFlags {
+  bool lw[W], rw[W];    // left / right wall node (bounce-back)
+  bool inactive[W];     // outside the lattice (bounce-back tiles only)
+};
+
+// For every lane, the value of the node to its left (right) in the tile: the thread's own previous
+// (next) lane, or the last (first) lane of the neighbouring thread from a per-thread shared array. At
+// the tile edges the lane's own value stands in (those nodes are never stored).
+template <typename X, int NT>
+__device__ __forceinline__ X left_of(const X* arr, int t, X own) {
+  if constexpr (Lane<X>::W == 1) {
+    return t > 0 ? arr[t - 1] : own;
+  } else {
+    return make_float2(t > 0 ? arr[t - 1].y : own.x, own.x);
+  }
+}
+template <typename X, int NT>
+__device__ __forceinline__ X right_of(const X* arr, int t, X own) {
+  if constexpr (Lane<X>::W == 1) {
+    return t < NT - 1 ? arr[t + 1] : own;
+  } else {
+    return make_float2(own.y, t < NT - 1 ? arr[t + 1].x : own.y);
+  }
+}
+
+// Rate-dependent lane constants of one lattice.
+template <typename X>
+struct AdjRates {
+  X s_e, s_psi, s_eps, one_m_se, one_m_sp, one_m_ss, q, s0, m_s0, gse;  // gse = -1/(4 s_e^2)
+};
+
+// One adjoint step of the thread's W nodes (every thread of the CTA calls it together; two CTA
+// barriers): from the forward states f = f(t) and a = a(t+1) to ao = a(t) and these nodes' terms of
+// dL/ds_e and dL/ds_psi. Valid where f and a are valid two nodes to each side. Every fused
+// multiply-add is explicit (fm), so paired lanes use FFMA2.
+template <typename X, int NT>
+__device__ __forceinline__ void adjoint_node_step(const X (&f)[6], const X (&a)[6], AdjShared<X, NT>& sh, int t,
+                                                  const NodeFlags<Lane<X>::W>& nf, const AdjRates<X>& rt_,
+                                                  const Consts<X>& c, X (&ao)[6], X& g_se, X& g_sp) {
+  const X zero = lit<X>(0.0);
+  // Phase 1: forward state of these nodes and their adjoint at t + 1.
+  Node<X> m;
+  node_state(f, c, rt_.s0, m);
+  sh.su[t] = m.u;
+  sh.sT[t] = m.T;
+  sh.sfp[t] = a[1]; sh.sgp[t] = a[4];
+  sh.sfm[t] = a[2]; sh.sgm[t] = a[5];
   __syncthreads();
 
-  // Phase 2: adjoint of the post-collision populations (transposed streaming).
-  R as[6];
+  // Phase 2: adjoint of the post-collision populations (transposed streaming): a+ from the right
+  // neighbour, a- from the left one; a wall node takes its own reflected one.
+  X as[6];
   as[0] = a[0];
   as[3] = a[3];
-  as[1] = rw ? a[2] : (n < NT - 1 ? sh.sap[n + 1][0] : R(0));
-  as[4] = rw ? a[5] : (n < NT - 1 ? sh.sap[n + 1][1] : R(0));
-  as[2] = lw ? a[1] : (n > 0 ? sh.sam[n - 1][0] : R(0));
-  as[5] = lw ? a[4] : (n > 0 ? sh.sam[n - 1][1] : R(0));
+  as[1] = sel<X>(nf.rw, a[2], right_of<X, NT>(sh.sfp, t, a[1]));
+  as[4] = sel<X>(nf.rw, a[5], right_of<X, NT>(sh.sgp, t, a[4]));
+  as[2] = sel<X>(nf.lw, a[1], left_of<X, NT>(sh.sfm, t, a[2]));
+  as[5] = sel<X>(nf.lw, a[4], left_of<X, NT>(sh.sgm, t, a[5]));
   // Transpose of M^{-1}: x0 = (r - q)/3, x+- = (2r + q)/6 +- j/2 per block.
-  const R rbf = (as[0] + as[1] + as[2]) * R(1.0 / 3.0), qbf = -as[0] * R(1.0 / 3.0) + (as[1] + as[2]) * R(1.0 / 6.0);
-  const R jbf = R(0.5) * (as[1] - as[2]);
-  const R rbg = (as[3] + as[4] + as[5]) * R(1.0 / 3.0), qbg = -as[3] * R(1.0 / 3.0) + (as[4] + as[5]) * R(1.0 / 6.0);
-  const R jbg = R(0.5) * (as[4] - as[5]);
-  R rt_b = rbf * c.inv_af, J_b = jbf * c.inv_af_l;
-  const R es_b = qbf * c.inv_af_l2;
-  R zt_b = rbg * c.inv_ag;
-  const R psis_b = jbg * c.inv_ag_l, epss_b = qbg * c.inv_ag_l2;
+  const X m_third = lit<X>(-1.0 / 3.0);
+  const X rbf = ml(ad(ad(as[0], as[1]), as[2]), c.third);
+  const X qbf = fm(as[0], m_third, ml(ad(as[1], as[2]), c.sixth));
+  const X jbf = ml(c.half, sb(as[1], as[2]));
+  const X rbg = ml(ad(ad(as[3], as[4]), as[5]), c.third);
+  const X qbg = fm(as[3], m_third, ml(ad(as[4], as[5]), c.sixth));
+  const X jbg = ml(c.half, sb(as[4], as[5]));
+  X rt_b = ml(rbf, c.inv_af), J_b = ml(jbf, c.inv_af_l);
+  const X es_b = ml(qbf, c.inv_af_l2);
+  X zt_b = ml(rbg, c.inv_ag);
+  const X psis_b = ml(jbg, c.inv_ag_l), epss_b = ml(qbg, c.inv_ag_l2);
 
-  // Forward quantities of the collision.
-  R ul = n > 0 ? sh.su[n - 1] : m.u, Tl = n > 0 ? sh.sT[n - 1] : m.T;
-  R ur = n < NT - 1 ? sh.su[n + 1] : m.u, Tr = n < NT - 1 ? sh.sT[n + 1] : m.T;
-  if (lw) { ul = -m.u; Tl = m.T; }
-  if (rw) { ur = -m.u; Tr = m.T; }
-  const R s = s0 + m.ds;
-  const R zeta = m.rho * s;
-  const R e_eq_t = R(3) * (m.J * m.u + m.pt) - c.two_lam2 * m.rt;
-  const R psi_eq = zeta * m.u;
+  // Forward quantities of the collision; wall ghosts u = -u0, T = T0.
+  X ul = left_of<X, NT>(sh.su, t, m.u), Tl = left_of<X, NT>(sh.sT, t, m.T);
+  X ur = right_of<X, NT>(sh.su, t, m.u), Tr = right_of<X, NT>(sh.sT, t, m.T);
+  const X neg_u = ml(m.u, c.m_one);
+  ul = sel<X>(nf.lw, neg_u, ul);
+  Tl = sel<X>(nf.lw, m.T, Tl);
+  ur = sel<X>(nf.rw, neg_u, ur);
+  Tr = sel<X>(nf.rw, m.T, Tr);
+  const X s = ad(rt_.s0, m.ds);
+  const X zeta = ml(m.rho, s);
+  const X e_eq_t = fm(c.m_two_lam2, m.rt, ml(c.three, fm(m.J, m.u, m.pt)));
+  const X psi_eq = ml(zeta, m.u);
 
   // Relaxation.
-  R et_b = (R(1) - s_e) * es_b, e_eq_b = s_e * es_b;
-  R psi_b = (R(1) - s_psi) * psis_b, psi_eq_b = s_psi * psis_b;
-  R epst_b = (R(1) - s_eps) * epss_b, eps_eq_b = s_eps * epss_b;
-  // Rate-gradient terms of this node in the arithmetic type.
-  g_se = es_b * (e_eq_t - m.et);
-  g_sp = psis_b * (psi_eq - m.psi);
+  const X et_b = ml(rt_.one_m_se, es_b);
+  X e_eq_b = ml(rt_.s_e, es_b);
+  const X psi_b = ml(rt_.one_m_sp, psis_b), psi_eq_b = ml(rt_.s_psi, psis_b);
+  const X epst_b = ml(rt_.one_m_ss, epss_b), eps_eq_b = ml(rt_.s_eps, epss_b);
+  g_se = ml(es_b, sb(e_eq_t, m.et));
+  g_sp = ml(psis_b, sb(psi_eq, m.psi));
 
-  R rho_b = R(0), ds_b = R(0), lnr_b = R(0), u_b = R(0), T_b = R(0), pt_b = R(0), ir_b = R(0);
-  R ul_b = R(0), ur_b = R(0), Tl_b = R(0), Tr_b = R(0);
+  X rho_b = zero, ds_b, lnr_b, u_b = zero, T_b = zero, pt_b, ir_b;
+  X ul_b = zero, ur_b = zero, Tl_b = zero, Tr_b = zero;
   // Source: zs = zt + S, S = q rho iT (du^2 + cP dT^2 iT); so far zt_b is the adjoint of zs.
   if (c.source_on) {
-    const R S_b = zt_b;
-    const R du = ur - ul, dT = Tr - Tl;
-    const R iT = m_rcp(m.T);
-    const R A = du * du + c.cp_over_Pr * dT * dT * iT;
-    rho_b += S_b * q * iT * A;
-    const R iT_b = S_b * q * m.rho * (A + c.cp_over_Pr * dT * dT * iT);
-    T_b -= iT_b * iT * iT;
-    const R du_b = S_b * q * m.rho * iT * R(2) * du;
-    const R dT_b = S_b * q * m.rho * iT * c.cp_over_Pr * R(2) * dT * iT;
-    ur_b = du_b; ul_b = -du_b; Tr_b = dT_b; Tl_b = -dT_b;
-    g_se += S_b * (m.rho * iT * A) * (R(-0.25) * m_rcp(s_e * s_e));
+    const X S_b = zt_b;
+    const X du = sb(ur, ul), dT = sb(Tr, Tl);
+    const X iT = m_rcp(m.T);
+    const X cdT2 = ml(c.cp_over_Pr, ml(dT, dT));
+    const X A = fm(cdT2, iT, ml(du, du));
+    const X Sq = ml(S_b, rt_.q);
+    rho_b = ml(ml(Sq, iT), A);
+    const X iT_b = ml(ml(Sq, m.rho), fm(cdT2, iT, A));
+    T_b = ml(ml(iT_b, iT), ml(iT, c.m_one));
+    const X Sqri2 = ml(ml(Sq, m.rho), ml(iT, c.two));
+    const X du_b = ml(Sqri2, du);
+    const X dT_b = ml(Sqri2, ml(ml(c.cp_over_Pr, dT), iT));
+    ur_b = du_b; ul_b = ml(du_b, c.m_one); Tr_b = dT_b; Tl_b = ml(dT_b, c.m_one);
+    g_se = fm(ml(S_b, ml(ml(m.rho, iT), A)), rt_.gse, g_se);
   }
-  // Walls: the ghosts are functions of this node's own u and T.
-  if (lw) { u_b -= ul_b; T_b += Tl_b; ul_b = R(0); Tl_b = R(0); }
-  if (rw) { u_b -= ur_b; T_b += Tr_b; ur_b = R(0); Tr_b = R(0); }
+  // Walls: the ghosts are functions of these nodes' own u and T.
+  u_b = sel<X>(nf.lw, sb(u_b, ul_b), u_b);
+  T_b = sel<X>(nf.lw, ad(T_b, Tl_b), T_b);
+  ul_b = sel<X>(nf.lw, zero, ul_b);
+  Tl_b = sel<X>(nf.lw, zero, Tl_b);
+  u_b = sel<X>(nf.rw, sb(u_b, ur_b), u_b);
+  T_b = sel<X>(nf.rw, ad(T_b, Tr_b), T_b);
+  ur_b = sel<X>(nf.rw, zero, ur_b);
+  Tr_b = sel<X>(nf.rw, zero, Tr_b);
   // eps_eq_t = 2 lam^2 rho (ds + cp_log lnr) + e_eq_t s + e_r ds.
-  rho_b += eps_eq_b * c.two_lam2 * (m.ds + c.cp_log * m.lnr);
-  ds_b += eps_eq_b * (c.two_lam2 * m.rho + c.e_r + e_eq_t);  // s = s0 + ds
-  lnr_b += eps_eq_b * c.two_lam2 * m.rho * c.cp_log;
-  e_eq_b += eps_eq_b * s;
+  const X ee2 = ml(eps_eq_b, c.two_lam2);
+  rho_b = fm(ee2, fm(c.cp_log, m.lnr, m.ds), rho_b);
+  ds_b = ml(eps_eq_b, ad(fm(c.two_lam2, m.rho, c.e_r), e_eq_t));
+  lnr_b = ml(ee2, ml(m.rho, c.cp_log));
+  e_eq_b = fm(eps_eq_b, s, e_eq_b);
   // psi_eq = zeta u with zeta = rho s.
-  const R zeta_b = psi_eq_b * m.u;
-  u_b += psi_eq_b * zeta;
-  rho_b += zeta_b * s;
-  ds_b += zeta_b * m.rho;
+  const X zeta_b = ml(psi_eq_b, m.u);
+  u_b = fm(psi_eq_b, zeta, u_b);
+  rho_b = fm(zeta_b, s, rho_b);
+  ds_b = fm(zeta_b, m.rho, ds_b);
   // e_eq_t = 3 (J u + pt) - 2 lam^2 rt.
-  J_b += R(3) * e_eq_b * m.u;
-  u_b += R(3) * e_eq_b * m.J;
-  pt_b += R(3) * e_eq_b;
-  rt_b -= c.two_lam2 * e_eq_b;
+  const X e3 = ml(c.three, e_eq_b);
+  J_b = fm(e3, m.u, J_b);
+  u_b = fm(e3, m.J, u_b);
+  pt_b = e3;
+  rt_b = fm(c.m_two_lam2, e_eq_b, rt_b);
 
   // Scatter the neighbours' source adjoints; only nodes of the lattice contribute.
-  sh.sul[n] = active ? ul_b : R(0);
-  sh.sur[n] = active ? ur_b : R(0);
-  sh.sTl[n] = active ? Tl_b : R(0);
-  sh.sTr[n] = active ? Tr_b : R(0);
-  __syncthreads();
-  // Phase 3: gather (node n - 1's right contribution and node n + 1's left one).
-  if (!lw && n > 0) { u_b += sh.sur[n - 1]; T_b += sh.sTr[n - 1]; }
-  if (!rw && n < NT - 1) { u_b += sh.sul[n + 1]; T_b += sh.sTl[n + 1]; }
+  {
+    const X ulv = sel<X>(nf.inactive, zero, ul_b), urv = sel<X>(nf.inactive, zero, ur_b);
+    const X Tlv = sel<X>(nf.inactive, zero, Tl_b), Trv = sel<X>(nf.inactive, zero, Tr_b);
+    sh.sul[t] = ulv;
+    sh.sur[t] = urv;
+    sh.sTl[t] = Tlv;
+    sh.sTr[t] = Trv;
+    __syncthreads();
+    // Phase 3: gather node i - 1's right contribution and node i + 1's left one (none across a wall).
+    const X gu = ad(sel<X>(nf.lw, zero, left_of<X, NT>(sh.sur, t, urv)), sel<X>(nf.rw, zero, right_of<X, NT>(sh.sul, t, ulv)));
+    const X gT = ad(sel<X>(nf.lw, zero, left_of<X, NT>(sh.sTr, t, Trv)), sel<X>(nf.rw, zero, right_of<X, NT>(sh.sTl, t, Tlv)));
+    u_b = ad(u_b, gu);
+    T_b = ad(T_b, gT);
+  }
 
   // Equation of state: T = (p0 + pt) ir / r, pt = p0 expm1(x), x = gamma (lnr + ds / cp).
-  pt_b += T_b * m.inv_rho * c.inv_r;
-  ir_b += T_b * (c.p0 + m.pt) * c.inv_r;
-  const R x_b = pt_b * (c.p0 + m.pt);
-  lnr_b += c.gamma * x_b;
-  ds_b += c.gamma * c.inv_cp * x_b;
+  const X p = ad(c.p0, m.pt);
+  pt_b = fm(ml(T_b, m.inv_rho), c.inv_r, pt_b);
+  ir_b = ml(ml(T_b, p), c.inv_r);
+  const X x_b = ml(pt_b, p);
+  lnr_b = fm(c.gamma, x_b, lnr_b);
+  ds_b = fm(ml(c.gamma, c.inv_cp), x_b, ds_b);
   // lnr = log1p(rt / rho0)
-  rt_b += lnr_b * m.inv_rho;
+  rt_b = fm(lnr_b, m.inv_rho, rt_b);
   // ds = (zt - rt s0) ir
-  zt_b += ds_b * m.inv_rho;
-  rt_b -= ds_b * s0 * m.inv_rho;
-  ir_b += ds_b * (m.zt - m.rt * s0);
+  const X dsi = ml(ds_b, m.inv_rho);
+  zt_b = ad(zt_b, dsi);
+  rt_b = fm(dsi, rt_.m_s0, rt_b);
+  ir_b = fm(ds_b, fm(m.rt, rt_.m_s0, m.zt), ir_b);
   // u = J ir
-  J_b += u_b * m.inv_rho;
-  ir_b += u_b * m.J;
+  J_b = fm(u_b, m.inv_rho, J_b);
+  ir_b = fm(u_b, m.J, ir_b);
   // ir = 1 / rho, rho = rho0 + rt
-  rho_b -= ir_b * m.inv_rho * m.inv_rho;
-  rt_b += rho_b;
+  rho_b = sb(rho_b, ml(ml(ir_b, m.inv_rho), m.inv_rho));
+  rt_b = ad(rt_b, rho_b);
   // Transpose of m = M f.
-  ao[0] = c.rho0 * rt_b - R(2) * c.af_l2 * et_b;
-  ao[1] = c.rho0 * rt_b + c.af_l * J_b + c.af_l2 * et_b;
-  ao[2] = c.rho0 * rt_b - c.af_l * J_b + c.af_l2 * et_b;
-  ao[3] = c.ag * zt_b - R(2) * c.ag_l2 * epst_b;
-  ao[4] = c.ag * zt_b + c.ag_l * psi_b + c.ag_l2 * epst_b;
-  ao[5] = c.ag * zt_b - c.ag_l * psi_b + c.ag_l2 * epst_b;
+  const X m2 = lit<X>(-2.0);
+  const X r0 = ml(c.rho0, rt_b), et2 = ml(c.af_l2, et_b);
+  ao[0] = fm(m2, et2, r0);
+  ao[1] = fm(c.af_l, J_b, ad(r0, et2));
+  ao[2] = fm(ml(c.af_l, c.m_one), J_b, ad(r0, et2));
+  const X z0 = ml(c.ag, zt_b), ep2 = ml(c.ag_l2, epst_b);
+  ao[3] = fm(m2, ep2, z0);
+  ao[4] = fm(c.ag_l, psi_b, ad(z0, ep2));
+  ao[5] = fm(ml(c.ag_l, c.m_one), psi_b, ad(z0, ep2));
 }
 
 // K adjoint steps per launch: a(t0 + K) -> a(t0), from the forward state f(t0) alone.
-// A CTA of NT threads owns NT consecutive nodes (one per thread). It first recomputes the forward
+// A CTA of NT threads owns TW = NT W consecutive nodes (W per thread). It first recomputes the forward
 // states f(t0), ..., f(t0 + K - 1) of its nodes on chip (the fused collide-stream update of the step
-// kernels, scalar lanes) and keeps them in shared memory, then runs the K reverse steps. The forward
-// step and the reverse step each reach two nodes, so f(t0 + k) is valid 2k nodes in from the tile
-// edges, a(t0 + k) 2K + 2(K - 1 - k) nodes in, and the tile stores its NT - 2(4K - 2) central nodes.
-// HBM traffic per node is one state and two adjoint reads/writes per K steps.
+// kernels) and keeps them in shared memory, then runs the K reverse steps. The forward step and the
+// reverse step each reach two nodes, so f(t0 + k) is valid 2k nodes in from the tile edges,
+// a(t0 + k) 2K + 2(K - 1 - k) nodes in, and the tile stores its TW - 2(4K - 2) central nodes. HBM
+// traffic per node is one state and two adjoint reads/writes per K steps.
 // The rate gradients dL/ds_e and dL/ds_psi of the stored nodes are summed per warp and step in the
 // arithmetic type, accumulated over the K steps in FP64 per warp, reduced over warps in a fixed order
 // and added to a per-tile accumulator only this tile's CTA touches (deterministic).
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) adjoint_block_kernel(const R* __restrict__ f0, const R* __restrict__ a_next,
-                                                           R* __restrict__ a_out, long long plane,
-                                                           const LatDev* __restrict__ lat, int B, long long ntiles, int K,
-                                                           Consts<R> c, double* __restrict__ grad_tile) {
+template <typename X, int NT>
+__global__ void __launch_bounds__(NT) adjoint_block_kernel(const typename Lane<X>::R* __restrict__ f0,
+                                                           const typename Lane<X>::R* __restrict__ a_next,
+                                                           typename Lane<X>::R* __restrict__ a_out, long long plane,
+                                                           const LatDev* __restrict__ lat, int B, long long ntiles,
+                                                           int K, Consts<X> c, double* __restrict__ grad_tile) {
+  using R = typename Lane<X>::R;
+  constexpr int W = Lane<X>::W, TW = NT * W, NW = NT / 32;
   extern __shared__ __align__(16) unsigned char adj_dyn[];
-  R* sf = reinterpret_cast<R*>(adj_dyn);  // [K][6][NT] forward states of this tile
-  __shared__ AdjShared<R, NT> sh;
-  const int n = threadIdx.x, lane = n & 31, warp = n >> 5;
+  X* sfx = reinterpret_cast<X*>(adj_dyn);  // [K][6][NT] forward states of this tile (one lane value per thread)
+  __shared__ AdjShared<X, NT> sh;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int halo = 4 * K - 2;
-  const int bout = NT - 2 * halo;
+  const int bout = TW - 2 * halo;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int L = 0;
     if (B > 1) {
@@ -180,79 +288,113 @@ __global__ void __launch_bounds__(NT) adjoint_block_kernel(const R* __restrict__
     }
     const LatDev d = lat[L];
     const long long N = d.n, off = d.offset;
-    const long long pos = (tile - d.tile0) * bout - halo + n;
-    long long lp = pos;
-    if (d.bc == 0) {
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-    } else {
-      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+    NodeFlags<W> nf;
+    long long pos[W], lp[W];
+    bool owned[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int i = t * W + j;
+      pos[j] = (tile - d.tile0) * bout - halo + i;
+      lp[j] = pos[j];
+      if (d.bc == 0) {
+        if (lp[j] < 0 || lp[j] >= N) { lp[j] %= N; if (lp[j] < 0) lp[j] += N; }
+      } else {
+        lp[j] = lp[j] < 0 ? 0 : (lp[j] >= N ? N - 1 : lp[j]);
+      }
+      const bool inside = pos[j] >= 0 && pos[j] < N;
+      nf.inactive[j] = d.bc != 0 && !inside;
+      nf.lw[j] = d.bc != 0 && pos[j] == 0;
+      nf.rw[j] = d.bc != 0 && pos[j] == N - 1;
+      owned[j] = i >= halo && i < halo + bout && inside;
     }
-    const bool inside = pos >= 0 && pos < N;
-    const bool active = d.bc == 0 || inside;
-    const bool lw = d.bc != 0 && pos == 0, rw = d.bc != 0 && pos == N - 1;
-    const bool owned = n >= halo && n < halo + bout && inside;
     const StepParams<R> P = step_params(d, R{});
-    const R m_s0h = -P.s0h, s0 = R(d.s0);
+    const X s_e = lit_r<X>(P.s_e), s_psi = lit_r<X>(P.s_psi), s_eps = lit_r<X>(P.s_eps);
+    const X q_src = lit_r<X>(P.q_src), s0h = lit_r<X>(P.s0h), m_s0h = lit_r<X>(-P.s0h);
+    const X le0 = lit_r<X>(P.lin_e0), lp0 = lit_r<X>(P.lin_p0), lq0 = lit_r<X>(P.lin_q0);
+    AdjRates<X> ar;
+    {
+      const R s0 = R(d.s0);
+      ar.s_e = s_e; ar.s_psi = s_psi; ar.s_eps = s_eps;
+      ar.one_m_se = lit_r<X>(R(1) - P.s_e);
+      ar.one_m_sp = lit_r<X>(R(1) - P.s_psi);
+      ar.one_m_ss = lit_r<X>(R(1) - P.s_eps);
+      ar.q = q_src;
+      ar.s0 = lit_r<X>(s0);
+      ar.m_s0 = lit_r<X>(-s0);
+      ar.gse = lit_r<X>(R(-0.25) * m_rcp(P.s_e * P.s_e));
+    }
 
     // Forward recompute: f(t0 + k) into shared memory, k = 0 .. K - 1.
-    R f[6];
+    X f[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) f[i] = f0[i * plane + off + lp];
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int j = 0; j < W; ++j) lset(f[q], j, f0[q * plane + off + lp[j]]);
     for (int k = 0; k < K; ++k) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) sf[(k * 6 + i) * NT + n] = f[i];
+      for (int q = 0; q < 6; ++q) sfx[(k * 6 + q) * NT + t] = f[q];
       if (k == K - 1) break;
-      NodeS<R> ms;
+      NodeS<X> ms;
       node_state_s(f, c, m_s0h, ms);
-      sh.su[n] = ms.u;
-      sh.sT[n] = ms.th;
+      sh.su[t] = ms.u;
+      sh.sT[t] = ms.th;
       __syncthreads();
-      R ul = n > 0 ? sh.su[n - 1] : ms.u, thl = n > 0 ? sh.sT[n - 1] : ms.th;
-      R ur = n < NT - 1 ? sh.su[n + 1] : ms.u, thr = n < NT - 1 ? sh.sT[n + 1] : ms.th;
-      if (lw) { ul = -ms.u; thl = ms.th; }
-      if (rw) { ur = -ms.u; thr = ms.th; }
-      R fs[6];
-      node_collide_s(ms, ul, ur, thl, thr, P.s_e, P.s_psi, P.s_eps, P.q_src, P.s0h, c, fs, P.lin_e0, P.lin_p0,
-                     P.lin_q0);
-      sh.sap[n][0] = fs[1]; sh.sap[n][1] = fs[4];
-      sh.sam[n][0] = fs[2]; sh.sam[n][1] = fs[5];
+      X ul = left_of<X, NT>(sh.su, t, ms.u), thl = left_of<X, NT>(sh.sT, t, ms.th);
+      X ur = right_of<X, NT>(sh.su, t, ms.u), thr = right_of<X, NT>(sh.sT, t, ms.th);
+      const X neg_u = ml(ms.u, c.m_one);
+      ul = sel<X>(nf.lw, neg_u, ul);
+      thl = sel<X>(nf.lw, ms.th, thl);
+      ur = sel<X>(nf.rw, neg_u, ur);
+      thr = sel<X>(nf.rw, ms.th, thr);
+      X fs[6];
+      node_collide_s(ms, ul, ur, thl, thr, s_e, s_psi, s_eps, q_src, s0h, c, fs, le0, lp0, lq0);
+      sh.sfp[t] = fs[1]; sh.sgp[t] = fs[4];
+      sh.sfm[t] = fs[2]; sh.sgm[t] = fs[5];
       __syncthreads();
+      // Streaming: f+, g+ from the left node, f-, g- from the right one; walls reflect their own.
       f[0] = fs[0];
       f[3] = fs[3];
-      f[1] = lw ? fs[2] : (n > 0 ? sh.sap[n - 1][0] : fs[1]);
-      f[4] = lw ? fs[5] : (n > 0 ? sh.sap[n - 1][1] : fs[4]);
-      f[2] = rw ? fs[1] : (n < NT - 1 ? sh.sam[n + 1][0] : fs[2]);
-      f[5] = rw ? fs[4] : (n < NT - 1 ? sh.sam[n + 1][1] : fs[5]);
+      f[1] = sel<X>(nf.lw, fs[2], left_of<X, NT>(sh.sfp, t, fs[1]));
+      f[4] = sel<X>(nf.lw, fs[5], left_of<X, NT>(sh.sgp, t, fs[4]));
+      f[2] = sel<X>(nf.rw, fs[1], right_of<X, NT>(sh.sfm, t, fs[2]));
+      f[5] = sel<X>(nf.rw, fs[4], right_of<X, NT>(sh.sgm, t, fs[5]));
     }
     __syncthreads();  // the reverse steps rewrite the exchange buffers
 
     // Reverse steps t0 + K - 1 .. t0.
-    R a[6];
+    X a[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) a[i] = a_next[i * plane + off + lp];
+    for (int q = 0; q < 6; ++q)
+#pragma unroll
+      for (int j = 0; j < W; ++j) lset(a[q], j, a_next[q * plane + off + lp[j]]);
     double acc_se = 0.0, acc_sp = 0.0;  // per warp (lane 0), over the K steps
     for (int k = K - 1; k >= 0; --k) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) f[i] = sf[(k * 6 + i) * NT + n];
-      R ao[6], g_se, g_sp;
-      adjoint_node_step<R, NT>(f, a, sh, n, lw, rw, active, P.s_e, P.s_psi, P.s_eps, P.q_src, s0, c, ao, g_se, g_sp);
+      for (int q = 0; q < 6; ++q) f[q] = sfx[(k * 6 + q) * NT + t];
+      X ao[6], gx_se, gx_sp;
+      adjoint_node_step<X, NT>(f, a, sh, t, nf, ar, c, ao, gx_se, gx_sp);
 #pragma unroll
-      for (int i = 0; i < 6; ++i) a[i] = ao[i];
-      if (!owned) { g_se = R(0); g_sp = R(0); }
+      for (int q = 0; q < 6; ++q) a[q] = ao[q];
+      R g_se = R(0), g_sp = R(0);
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (owned[j]) { g_se += lget(gx_se, j); g_sp += lget(gx_sp, j); }
       for (int o = 16; o > 0; o >>= 1) {
         g_se += __shfl_down_sync(0xffffffffu, g_se, o);
         g_sp += __shfl_down_sync(0xffffffffu, g_sp, o);
       }
       if (lane == 0) { acc_se += (double)g_se; acc_sp += (double)g_sp; }
     }
-    if (owned)
 #pragma unroll
-      for (int i = 0; i < 6; ++i) a_out[i * plane + off + pos] = a[i];
+    for (int j = 0; j < W; ++j)
+      if (owned[j])
+#pragma unroll
+        for (int q = 0; q < 6; ++q) a_out[q * plane + off + pos[j]] = lget(a[q], j);
     if (lane == 0) { sh.sg[0][warp] = acc_se; sh.sg[1][warp] = acc_sp; }
     __syncthreads();
-    if (n == 0) {
+    if (t == 0) {
       double t0 = 0.0, t1 = 0.0;
-      for (int w = 0; w < NT / 32; ++w) { t0 += sh.sg[0][w]; t1 += sh.sg[1][w]; }
+      for (int w = 0; w < NW; ++w) { t0 += sh.sg[0][w]; t1 += sh.sg[1][w]; }
       grad_tile[2 * tile] += t0;
       grad_tile[2 * tile + 1] += t1;
     }
@@ -386,25 +528,36 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, long long n, d
   }
 }
 
-template <typename R>
-cudaError_t launch_adjoint_block(const R* f0, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
-                                 long long ntiles, int K, const Consts<R>& c, double* grad_tile, cudaStream_t st) {
-  if (ntiles <= 0) return cudaSuccess;
-  if (K < 1 || K > kAdjointMaxK) return cudaErrorInvalidValue;
+// FP64 runs one node per thread; FP32 two per thread on paired lanes. Both tile kAdjointThreads nodes.
+template <typename X>
+static cudaError_t launch_block_lanes(const typename Lane<X>::R* f0, const typename Lane<X>::R* a_next,
+                                      typename Lane<X>::R* a_out, long long plane, const LatDev* lat, int B,
+                                      long long ntiles, int K, const Consts<X>& c, double* grad_tile, cudaStream_t st) {
+  using R = typename Lane<X>::R;
+  constexpr int NT = kAdjointThreads / Lane<X>::W;
   const size_t dyn = (size_t)kAdjointMaxK * 6 * kAdjointThreads * sizeof(R);
-  static bool attr_set[2] = {false, false};  // per arithmetic type, once per process (the limit is per function)
-  bool& done = attr_set[sizeof(R) == 8];
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_block_kernel<R, kAdjointThreads>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  static bool attr_set = false;  // once per lane type and process (the limit is per function)
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_block_kernel<X, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
     if (e != cudaSuccess) return e;
-    done = true;
+    attr_set = true;
   }
   const size_t use = (size_t)K * 6 * kAdjointThreads * sizeof(R);
-  adjoint_block_kernel<R, kAdjointThreads><<<(unsigned)ntiles, kAdjointThreads, use, st>>>(f0, a_next, a_out, plane,
-                                                                                          lat, B, ntiles, K, c,
-                                                                                          grad_tile);
+  adjoint_block_kernel<X, NT><<<(unsigned)ntiles, NT, use, st>>>(f0, a_next, a_out, plane, lat, B, ntiles, K, c,
+                                                                 grad_tile);
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_adjoint_block(const R* f0, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
+                                 long long ntiles, int K, const ConstSet<R>& c, double* grad_tile, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (K < 1 || K > kAdjointMaxK) return cudaErrorInvalidValue;
+  if constexpr (sizeof(R) == 4)
+    return launch_block_lanes<float2>(f0, a_next, a_out, plane, lat, B, ntiles, K, c.p, grad_tile, st);
+  else
+    return launch_block_lanes<double>(f0, a_next, a_out, plane, lat, B, ntiles, K, c.s, grad_tile, st);
 }
 
 cudaError_t launch_reduce_rate_grads(const double* grad_tile, const LatDev* lat, int B, long long ntiles, double* out,
@@ -444,9 +597,9 @@ template cudaError_t launch_to_f64<float>(const float*, double*, long long, cuda
 template cudaError_t launch_to_f64<double>(const double*, double*, long long, cudaStream_t);
 
 template cudaError_t launch_adjoint_block<float>(const float*, const float*, float*, long long, const LatDev*, int,
-                                                 long long, int, const Consts<float>&, double*, cudaStream_t);
+                                                 long long, int, const ConstSet<float>&, double*, cudaStream_t);
 template cudaError_t launch_adjoint_block<double>(const double*, const double*, double*, long long, const LatDev*, int,
-                                                  long long, int, const Consts<double>&, double*, cudaStream_t);
+                                                  long long, int, const ConstSet<double>&, double*, cudaStream_t);
 template cudaError_t launch_adjoint_init<float>(const float*, const float*, long long, const LatDev*, int,
                                                 const Consts<double>&, double*, double*, cudaStream_t);
 template cudaError_t launch_adjoint_init<double>(const double*, const double*, long long, const LatDev*, int,

@@ -1127,7 +1127,7 @@ int adjoint_reverse(lbm_ctx* c, int* res) {
       const int Kb = (int)std::min<long long>(KA, len - b * KA);
       cudaError_t e = lbm::launch_adjoint_block<R>(st[b], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot,
                                                    c->d_lat_adj + (size_t)(Kb - 1) * c->B, c->B,
-                                                   c->adj_ntiles[Kb - 1], Kb, k.s, c->d_gtile[Kb - 1], c->stream);
+                                                   c->adj_ntiles[Kb - 1], Kb, k, c->d_gtile[Kb - 1], c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
       a = 1 - a;
     }

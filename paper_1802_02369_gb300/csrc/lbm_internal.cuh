@@ -374,7 +374,7 @@ constexpr int kAdjointMaxK = 8;
 inline int adjoint_tile_out(int K) { return kAdjointThreads - 2 * (4 * K - 2); }
 template <typename R>
 cudaError_t launch_adjoint_block(const R* f0, const R* a_next, R* a_out, long long plane, const LatDev* lat, int B,
-                                 long long ntiles, int K, const Consts<R>& c, double* grad_tile, cudaStream_t st);
+                                 long long ntiles, int K, const ConstSet<R>& c, double* grad_tile, cudaStream_t st);
 cudaError_t launch_reduce_rate_grads(const double* grad_tile, const LatDev* lat, int B, long long ntiles, double* out,
                                      bool accumulate, cudaStream_t st);
 template <typename R>
