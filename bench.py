@@ -45,6 +45,10 @@ FLOPS_PER_NODE = {"f32": 118.0, "f64": (2 * 507.31008e6 + 194.468864e6 + 194.468
 # Peak arithmetic per SM per clock from the unit counts: 128 FP32 FMA lanes (256 flops); FP64 at
 # 2 FMA per SM per clock (4 flops; the nominal 1.25 TFLOP/s of the part at 152 SMs, 2.07 GHz).
 FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
+# FP32 operations (FADD + FMUL + FFMA, each one lane-operation) per computed node-step of the
+# double-float step kernel, from ncu at N = 2^23, (8, 256, 1): (49,009,766,400 FADD + 13,958,963,200
+# FFMA + 4,831,948,800 FMUL) over 37,450 x 256 x 8 node-steps = 884.0 (profiles/step_tiles_df_N8M.md).
+DF_FP32_OPS_PER_COMPUTED = 67800678400 / 76697600
 TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.499136e6 + 147.712768e6) / 8388608,
                           ("f64", 1, 256, 2): (403.403008e6 + 347.594752e6) / 8388608}
 
@@ -255,6 +259,80 @@ def run_batched(args, lbm, torch, hbm_peak, world):
                          "effective_frac": glups / world * BYTES_PER_NODE["f32"] / hbm_peak}}
 
 
+def run_sweep(args, lbm, torch):
+    """Precision and scale sweep: 64 lattices of 2^20 nodes, steepening wave of amplitude 0.2, lattice b
+    with s_e = (1.2, 1.6, 1.9)[b mod 3], FP32 shifted populations and FP64, autotuned. Reported per
+    precision: GLUPS over the timed steps, the per-step drift of the mass and momentum sums over the
+    first 100 steps, |sum(t) - sum(0)| / (t sum rho(0)), and the lattices flagged at the end (the
+    scheme is linearly unstable at |u| = 0.2: every lattice blows up from rounding noise within a few
+    hundred steps; the accuracy against the oracle is a parity test, not a bench figure)."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    B, N = 64, 1 << 20
+    s_vals = np.array([1.2, 1.6, 1.9])
+    s_e = s_vals[np.arange(B) % 3]
+    rho, u, p = W.steepening_wave(N, 0.2, W.reference_pressure())
+    fields = [torch.from_numpy(np.tile(x, B)).cuda() for x in (rho, u, p)]
+    out = {}
+    for prec, steps in (("f32", 2000), ("f64", 200)):
+        lat = lbm.Lattice(np.full(B, N), s_e=s_e, precision=prec)
+        lat.set_state(*fields)
+        k, nt, v = lat.autotune(1)
+        lat.set_state(*fields)
+        s0, _, _ = lat.diagnostics()
+        lat.step(100)
+        s1, _, _ = lat.diagnostics()
+        drift = np.abs(s1[:, :2] - s0[:, :2]).max(axis=0) / (100 * s0[:, 0].max())
+        steps = (steps // k) * k
+        lat.set_state(*fields)
+        ms = time_device(lat, torch, steps, 3 * k, None, 1)
+        _, flags, _ = lat.diagnostics()
+        lat.close()
+        out[prec] = {"value": B * N * steps / (ms * 1e-3) / 1e9, "unit": UNIT, "lattices": B, "N": N,
+                     "steps": steps, "steps_per_launch": k, "block_threads": nt, "nodes_per_thread": v,
+                     "mass_drift_per_step": float(drift[0]), "momentum_drift_per_step": float(drift[1]),
+                     "lattices_flagged_at_end": int((flags != 0).sum())}
+    del fields
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_df(args, lbm, torch, N: int, sm_clock_mhz: float):
+    """The benchmark workload with FP64 storage and the time step in double-float on the FP32 pipes
+    (precision LBM_F64_DF), autotuned, beside the native FP64 figure."""
+    rho, u, p = workload_fields(N)
+    d = [torch.from_numpy(x).cuda() for x in (rho, u, p)]
+    lat = lbm.Lattice(N, s_e=S_E, precision="f64df")
+    lat.set_state(*d)
+    if args.df_config:
+        lat.set_config(*[int(x) for x in args.df_config.split(",")])
+        k, nt, v = lat.get_config()
+    else:
+        k, nt, v = lat.autotune(2)
+    lat.set_state(*d)
+    steps = max(k, (args.df_steps // k) * k)
+    ms = time_device(lat, torch, steps, 3 * k, None, 1)
+    _, flags, _ = lat.diagnostics()
+    lat.close()
+    del d
+    torch.cuda.empty_cache()
+    glups = N * steps / (ms * 1e-3) / 1e9
+    r = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": k, "block_threads": nt,
+         "nodes_per_thread": v, "launch_ms": ms / (steps // k), "flags": int(flags[0]),
+         "arithmetic": "double-float (two FP32 numbers per value) on the FP32 pipes, FP64 storage",
+         "effective_gbs": glups * BYTES_PER_NODE["f64"]}
+    if DF_FP32_OPS_PER_COMPUTED is not None:
+        ops = DF_FP32_OPS_PER_COMPUTED * nt * v / (nt * v - 4 * k)
+        a = glups * ops / 1e3
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        pk = props.multi_processor_count * 128 * sm_clock_mhz * 1e6 / 1e12
+        r["roofline"] = {"bound": "alu", "achieved": a, "peak": pk, "unit": "T FP32 op/s", "frac": a / pk,
+                         "fp32_ops_per_node_update": ops,
+                         "peak_kind": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
+                                      f"{sm_clock_mhz:.0f} MHz (one operation per lane per clock)"}
+    return r
+
+
 def run_linear(args, lbm, torch):
     """The section 7 linear scheme (linear equilibria around u0 = 0.15, s0 = 0.2, sigma_eps = 1.5,
     no source) on a small acoustic wave, N = 2^26, autotuned, FP32 and FP64."""
@@ -456,6 +534,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     torch.cuda.set_device(local)
     build.build()
     hbm_peak, peak_kind = measured_peaks()
+    if args.df_only:
+        with ClockSampler(local) as clk:
+            res = run_df(args, lbm, torch, args.nodes, 2070.0)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "double-float", "nodes": args.nodes, "results": res,
+                              "clocks": clk.summary()}), flush=True)
+        return
     if args.adjoint_only:
         res = run_adjoint(args, lbm, torch)
         if rank == 0:
@@ -535,6 +620,8 @@ def run_ours(args, rank: int, world: int, local: int, dist):
 
     batched = None if args.no_batched else run_batched(args, lbm, torch, hbm_peak, world)
     linear = None if args.no_linear else run_linear(args, lbm, torch)
+    sweep = None if args.no_sweep else run_sweep(args, lbm, torch)
+    dfl = None if args.no_df else run_df(args, lbm, torch, N_NODES, clocks.get("sm_max_mhz") or 2070.0)
     adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch)
     fdiff = None if args.no_fd else run_fd(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
     d1q3 = None if args.no_d1q3 else run_d1q3(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
@@ -582,12 +669,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                        "l2": "inputs larger than L2 (FP32 state 1.6 GB, FP64 3.2 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof_alu(f32, "f32"), "roofline_hbm": roof(f32, "f32"),
+            "fp64_double_float": dfl,
             "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"], "steps": f64["steps"],
                      "steps_per_launch": f64["k"], "block_threads": f64["block_threads"],
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
                      "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
-            "finite_differences": fdiff, "d1q3_schemes": d1q3,
+            "finite_differences": fdiff, "d1q3_schemes": d1q3, "precision_sweep": sweep,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"], "clocks": clocks,
             "diagnostic_flags": {"f32": f32["flags"], "f64": f64["flags"]}}
     print(json.dumps(line), flush=True)
@@ -616,6 +704,11 @@ def main():
     ap.add_argument("--fd-config", default="", help="k,block_threads,nodes_per_thread of the finite-difference kernel")
     ap.add_argument("--fd-steps-f64", type=int, default=200)
     ap.add_argument("--fd-steps-f32", type=int, default=1000)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-df", action="store_true")
+    ap.add_argument("--df-only", action="store_true", help="only the double-float leg at --nodes")
+    ap.add_argument("--df-config", default="", help="k,block_threads,nodes_per_thread of the double-float kernel")
+    ap.add_argument("--df-steps", type=int, default=200)
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint leg")
     ap.add_argument("--adjoint-lattices", type=int, default=256)
     ap.add_argument("--no-d1q3", action="store_true")

@@ -54,8 +54,14 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
 /* Storage/arithmetic precision of the populations.
  * LBM_F64: FP64 storage and arithmetic.
  * LBM_F32_SHIFTED: FP32 storage and arithmetic of the shifted populations f - w, where w are the
- *   populations of the rest state (rho0, u = 0, s = s0) (the same shift is used in FP64). */
-enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1 };
+ *   populations of the rest state (rho0, u = 0, s = s0) (the same shift is used in FP64).
+ * LBM_F64_DF: FP64 storage of the shifted populations; the time step computes in double-float (each
+ *   value an unevaluated sum of two FP32 numbers, about 48 significant bits) on the FP32 pipes, which
+ *   GB300 runs far faster than its FP64 pipe. Same results as LBM_F64 to about 1e-13 relative; the
+ *   remaining kernels (initialisation, moments, diagnostics, the adjoint) run in FP64 as for LBM_F64.
+ *   Only LBM_MODE_LAUNCH; kernel configurations: steps_per_launch in {1, 2, 4, 8}, block_threads in
+ *   {128, 256, 512}, nodes_per_thread in {1, 2}. */
+enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F64_DF = 2 };
 
 /* Relaxation rates of step (iii). s_e is the free rate (eq. henon-d1q3q3, nu = sigma_e lambda dx).
  * s_psi <= 0 selects the coupling of eq. (lien-sigma-sigma), sigma_psi = (3/2)(gamma/Pr) sigma_e.
@@ -171,6 +177,12 @@ int lbm_debug_persistent(lbm_ctx *ctx, int64_t spin_limit, int64_t withhold_tile
  * 1 = log(1+x) on single lanes (CUDA's log1pf), 2 = exp(x)-1 on paired lanes, 3 = exp(x)-1 on
  * single lanes (CUDA's expm1f), 4 = the FP32 reciprocal. */
 int lbm_debug_eval_f32(const float *x, float *y, int64_t n, int32_t fn, void *stream);
+
+/* Test hook: the double-float operations of the LBM_F64_DF step, elementwise on n doubles (device
+ * pointers, enqueued on stream), each input split into hi + lo floats and the result summed back to
+ * FP64: fn 0 = log(1+x), 1 = exp(x)-1, 2 = 1/x, 3 = x*x2, 4 = x+x2, 5 = x*x2[i] + x2[(i+1) mod n]
+ * (x2 unused and may be NULL for fn 0-2). */
+int lbm_debug_eval_df(const double *x, const double *x2, double *y, int64_t n, int32_t fn, void *stream);
 
 /* Times every valid (k, block_threads, nodes_per_thread) on the current state (which is left
  * unchanged; each trial writes only the second buffer, over at most 16384 tiles) and keeps the

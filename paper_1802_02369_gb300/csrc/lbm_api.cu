@@ -15,6 +15,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_internal.cuh"
+#include "lbm_df.cuh"
 
 using lbm::Consts;
 using lbm::LatDev;
@@ -50,6 +51,7 @@ struct PhysD {
 template <typename X>
 X lift(double v) {
   if constexpr (std::is_same<X, float2>::value) return make_float2((float)v, (float)v);
+  else if constexpr (std::is_same<X, lbm::df>::value) return lbm::df_from_double_host(v);
   else return X(v);
 }
 
@@ -413,7 +415,8 @@ struct lbm_ctx {
   double* d_lpart = nullptr;
   double* d_loss = nullptr;
 
-  size_t elem() const { return precision == LBM_F64 ? sizeof(double) : sizeof(float); }
+  bool f64() const { return precision != LBM_F32_SHIFTED; }  // FP64 storage (LBM_F64, LBM_F64_DF)
+  size_t elem() const { return f64() ? sizeof(double) : sizeof(float); }
   size_t state_bytes() const { return 6 * (size_t)Ntot * elem(); }
 };
 
@@ -521,7 +524,7 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   if (!out) return LBM_ERR_INVALID_ARG;
   *out = nullptr;
   if (B < 1 || !N || !rates || !bc || !(lambda > 0.0) || !std::isfinite(lambda)) return LBM_ERR_INVALID_ARG;
-  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED) return LBM_ERR_INVALID_ARG;
+  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED && precision != LBM_F64_DF) return LBM_ERR_INVALID_ARG;
   PhysD ph;
   ph.lam = lambda;
   ph.gamma = phys ? phys->gamma : 1.4;
@@ -595,16 +598,20 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
     d.pad = 0;
     {
       const double v[8] = {d.s_e, d.s_psi, d.s_eps, d.q_src, d.s0h, d.lin_e0, d.lin_p0, d.lin_q0};
-      for (int i = 0; i < 8; ++i) d.f32[i] = (float)v[i];  // round to nearest, as the device conversion
+      for (int i = 0; i < 8; ++i) {
+        d.f32[i] = (float)v[i];  // round to nearest, as the device conversion
+        d.f32lo[i] = (float)(v[i] - (double)d.f32[i]);
+      }
     }
     tot += N[b];
   }
   c->offset[B] = tot;
   c->Ntot = tot;
-  c->K = (precision == LBM_F64) ? 1 : 4;
-  c->adj_K = (precision == LBM_F64) ? 1 : 4;  // measured fastest (FP64 is bound by its arithmetic)
-  c->NT = (precision == LBM_F64) ? 512 : 256;
-  c->V = (precision == LBM_F64) ? 1 : 2;
+  const bool f32 = precision == LBM_F32_SHIFTED;
+  c->K = precision == LBM_F64 ? 1 : 4;
+  c->adj_K = f32 ? 4 : 1;  // measured fastest (FP64 is bound by its arithmetic)
+  c->NT = precision == LBM_F64 ? 512 : 256;
+  c->V = f32 ? 2 : 1;
   rebuild_tables(c);
 
   c->d_lat = (LatDev*)dev_alloc(sizeof(LatDev) * 4 * B, c->stream);
@@ -702,6 +709,30 @@ int run_steps(lbm_ctx* c, long long nsteps) {
   return LBM_OK;
 }
 
+// Double-float arithmetic on FP64 storage (LBM_F64_DF): one launch per K steps.
+int run_steps_df(lbm_ctx* c, long long nsteps) {
+  const Consts<lbm::df> k = make_consts<lbm::df>(c->ph);
+  long long left = nsteps;
+  while (left > 0) {
+    int K = c->K;
+    while (K > left) K >>= 1;
+    const int ki = depth_index(K);
+    cudaError_t e = lbm::launch_step_tiles_df((const double*)c->state[c->cur], (double*)c->state[1 - c->cur], c->Ntot,
+                                              lat_for(c, K), tile_map_for(c, K), c->B, c->ntiles_k[ki], K, c->NT,
+                                              c->V, k, c->stream, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "double-float step kernel launch");
+    c->cur = 1 - c->cur;
+    left -= K;
+    c->steps_done += K;
+  }
+  return LBM_OK;
+}
+
+bool valid_config(const lbm_ctx* c, int K, int NT, int V) {
+  if (c->precision == LBM_F64_DF) return lbm::valid_df_config(K, NT, V);
+  return lbm::valid_tile_config(K, NT, V, c->precision == LBM_F64);
+}
+
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int set_state_impl(lbm_ctx* c, const double* rho, const double* u, const double* x, int from_p) {
@@ -723,7 +754,7 @@ int set_state_impl(lbm_ctx* c, const double* rho, const double* u, const double*
     dx = c->d_stage + 2 * n;
   }
   const InitArgs a = init_args(c);
-  if (c->precision == LBM_F64)
+  if (c->f64())
     init_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(dr, du, dx, from_p, (double*)c->state[c->cur], n,
                                                                     c->d_lat, c->B, a);
   else
@@ -805,6 +836,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps) {
   if (!c) return LBM_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "step: nsteps < 0");
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "step: no state set");
+  if (c->precision == LBM_F64_DF) return run_steps_df(c, nsteps);
   return c->precision == LBM_F64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
 }
 
@@ -833,7 +865,7 @@ int lbm_moments(lbm_ctx* c, double* rho, double* J, double* zeta, double* e, dou
     for (int i = 0; i < 6; ++i) dst[i] = outs[i];
   }
   const InitArgs a = init_args(c);
-  if (c->precision == LBM_F64)
+  if (c->f64())
     moments_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->d_lat, c->B,
                                                                        a, dst[0], dst[1], dst[2], dst[3], dst[4], dst[5]);
   else
@@ -860,7 +892,7 @@ int lbm_get_populations(lbm_ctx* c, double* fd) {
     dst = c->d_stage;
   }
   const double wf0 = c->ph.wf0(), wf1 = c->ph.wf1();
-  if (c->precision == LBM_F64)
+  if (c->f64())
     pops_out_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->d_lat,
                                                                         c->B, wf0, wf1, dst);
   else
@@ -886,7 +918,7 @@ int lbm_set_populations(lbm_ctx* c, const double* fd) {
     src = c->d_stage;
   }
   const double wf0 = c->ph.wf0(), wf1 = c->ph.wf1();
-  if (c->precision == LBM_F64)
+  if (c->f64())
     pops_in_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((double*)c->state[c->cur], n, c->d_lat, c->B, wf0,
                                                                        wf1, src);
   else
@@ -906,7 +938,7 @@ int lbm_diagnostics(lbm_ctx* c, double* sums, int32_t* flags) {
   const InitArgs a = init_args(c);
   const double inv_r = 1.0 / c->ph.r();
   if (c->nchunks > 0) {
-    if (c->precision == LBM_F64)
+    if (c->f64())
       diag_chunk_kernel<double><<<(unsigned)c->nchunks, kDiagThreads, 0, c->stream>>>(
           (const double*)c->state[c->cur], c->Ntot, c->d_lat, c->B, a, c->ph.gamma, inv_r, c->d_part, c->d_pflag);
     else
@@ -929,7 +961,7 @@ int lbm_diagnostics(lbm_ctx* c, double* sums, int32_t* flags) {
 int lbm_set_config(lbm_ctx* c, int32_t k, int32_t nt, int32_t v) {
   if (!c) return LBM_ERR_INVALID_ARG;
   const int newK = k ? k : c->K, newNT = nt ? nt : c->NT, newV = v ? v : c->V;
-  if (!lbm::valid_tile_config(newK, newNT, newV, c->precision == LBM_F64))
+  if (!valid_config(c, newK, newNT, newV))
     return fail(c, LBM_ERR_INVALID_ARG, "config: unsupported (steps_per_launch, block_threads, nodes_per_thread)");
   c->K = newK;
   c->NT = newNT;
@@ -962,7 +994,7 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
   for (int nt : NTs)
     for (int v : Vs)
       for (int k : Ks) {
-        if (!lbm::valid_tile_config(k, nt, v, c->precision == LBM_F64)) continue;
+        if (!valid_config(c, k, nt, v)) continue;
         c->K = k;
         c->NT = nt;
         c->V = v;
@@ -975,7 +1007,11 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
         for (int t = 0; t <= trials; ++t) {  // the first launch is a warm-up
           if (t == 1) LBM_CK(c, cudaEventRecord(e0, c->stream));
           cudaError_t e;
-          if (c->precision == LBM_F64)
+          if (c->precision == LBM_F64_DF)
+            e = lbm::launch_step_tiles_df((const double*)c->state[c->cur], (double*)c->state[1 - c->cur], c->Ntot,
+                                          lat_for(c, k), tile_map_for(c, k), c->B, nt_run, k, nt, v,
+                                          make_consts<lbm::df>(c->ph), c->stream, 0);
+          else if (c->f64())
             e = lbm::launch_step_tiles<double>((const double*)c->state[c->cur], (double*)c->state[1 - c->cur],
                                                c->Ntot, lat_for(c, k), tile_map_for(c, k), c->B, nt_run, k, nt, v,
                                                make_constset<double>(c->ph), c->stream, 0);
@@ -1004,6 +1040,8 @@ int lbm_set_mode(lbm_ctx* c, int32_t mode) {
   if (!c) return LBM_ERR_INVALID_ARG;
   if (mode != LBM_MODE_LAUNCH && mode != LBM_MODE_PERSISTENT && mode != LBM_MODE_PERSISTENT_GRAPH)
     return fail(c, LBM_ERR_INVALID_ARG, "set_mode: unknown mode");
+  if (mode != LBM_MODE_LAUNCH && c->precision == LBM_F64_DF)
+    return fail(c, LBM_ERR_INVALID_ARG, "set_mode: double-float contexts run one launch per block");
   c->mode = mode;
   return LBM_OK;
 }
@@ -1191,14 +1229,14 @@ int lbm_adjoint_forward(lbm_ctx* c, int64_t T) {
   if (!c || T < 1) return LBM_ERR_INVALID_ARG;
   if (c->ph.eq_mode != 0) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: only the nonlinear equilibria are differentiated");
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "adjoint: no state set");
-  return c->precision == LBM_F64 ? adjoint_forward_impl<double>(c, T) : adjoint_forward_impl<float>(c, T);
+  return c->f64() ? adjoint_forward_impl<double>(c, T) : adjoint_forward_impl<float>(c, T);
 }
 
 int lbm_adjoint_backward(lbm_ctx* c, const double* dL_drho_T, double* dL_drho0, double* dL_du0, double* dL_drates,
                          double* dL_dfd0) {
   NvtxRange r("lbm_adjoint_backward");
   if (!c || !dL_drho_T) return LBM_ERR_INVALID_ARG;
-  return c->precision == LBM_F64
+  return c->f64()
              ? adjoint_backward_impl<double>(c, nullptr, dL_drho_T, nullptr, dL_drho0, dL_du0, dL_drates, dL_dfd0)
              : adjoint_backward_impl<float>(c, nullptr, dL_drho_T, nullptr, dL_drho0, dL_du0, dL_drates, dL_dfd0);
 }
@@ -1208,7 +1246,7 @@ int lbm_adjoint(lbm_ctx* c, int64_t T, const double* rho_target, double* loss, d
   if (!c || !rho_target || T < 1) return LBM_ERR_INVALID_ARG;
   int rc = lbm_adjoint_forward(c, T);
   if (rc) return rc;
-  return c->precision == LBM_F64
+  return c->f64()
              ? adjoint_backward_impl<double>(c, rho_target, nullptr, loss, dL_drho0, dL_du0, dL_drates, nullptr)
              : adjoint_backward_impl<float>(c, rho_target, nullptr, loss, dL_drho0, dL_du0, dL_drates, nullptr);
 }
@@ -1230,7 +1268,7 @@ int lbm_adjoint_release(lbm_ctx* c) {
 
 int lbm_adjoint_set_config(lbm_ctx* c, int32_t steps_per_launch) {
   if (!c) return LBM_ERR_INVALID_ARG;
-  const int K = steps_per_launch > 0 ? steps_per_launch : (c->precision == LBM_F64 ? 1 : 4);
+  const int K = steps_per_launch > 0 ? steps_per_launch : (c->f64() ? 1 : 4);
   if (K != 1 && K != 2 && K != 4 && K != 8)
     return fail(c, LBM_ERR_INVALID_ARG, "adjoint_set_config: steps_per_launch must be 1, 2, 4 or 8");
   c->adj_K = K;

@@ -22,8 +22,10 @@ struct LatDev {
   double lin_e0, lin_p0, lin_q0;  // constant terms of the linear equilibria in scaled moments
   int bc, pad;
   // s_e, s_psi, s_eps, q_src, s0h, lin_e0, lin_p0, lin_q0 rounded to FP32 on the host, for the FP32
-  // kernels (a double-to-float conversion on the device runs on the slow FP64 pipe).
+  // kernels (a double-to-float conversion on the device runs on the slow FP64 pipe), and the low parts
+  // v - (float)v of the same eight values for the double-float kernels (value = f32[i] + f32lo[i]).
   float f32[8];
+  float f32lo[8];
 };
 
 // The per-lattice parameters of the step kernels in the arithmetic type R.

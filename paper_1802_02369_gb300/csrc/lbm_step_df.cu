@@ -1,0 +1,157 @@
+// Fused collide-stream step of the D1Q3Q3 scheme (section 8, steps (i)-(viii)) with FP64 storage and
+// double-float arithmetic on the FP32 pipes (precision LBM_F64_DF).
+//
+// The same temporally blocked tile update as the step kernels of lbm_step.cu (tiles of NT*V nodes,
+// thread t holding nodes tV .. tV+V-1, K steps on chip, 2K halo nodes recomputed per side), with every
+// node value a double-float (lbm_df.cuh): the populations are split into hi + lo floats when the tile is
+// loaded, the dimensionless node update of lbm_internal.cuh runs on df lanes, and the populations are
+// summed back to FP64 when the tile is stored. Neighbour values cross threads by two shuffles (hi, lo)
+// and warps through shared memory.
+#include "lbm_df.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ df shfl_up(df v) {
+  return df{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+__device__ __forceinline__ df shfl_down(df v) {
+  return df{__shfl_down_sync(0xffffffffu, v.hi, 1), __shfl_down_sync(0xffffffffu, v.lo, 1)};
+}
+__device__ __forceinline__ df neg(df v) { return df{-v.hi, -v.lo}; }
+
+template <int NT, int V, bool WALLS>
+__device__ __forceinline__ void tile_body_df(const double* __restrict__ in, double* __restrict__ out,
+                                             long long plane, const LatDev& d, long long start, int K,
+                                             const Consts<df>& c, df (*e_ut)[4], df (*e_f)[4]) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int halo = 2 * K;
+  const int bout = NT * V - 2 * halo;
+  const long long off = d.offset, N = d.n;
+  // Per-lattice parameters split into hi + lo on the host (no FP64-pipe conversion per tile).
+  const df s_e{d.f32[0], d.f32lo[0]}, s_psi{d.f32[1], d.f32lo[1]}, s_eps{d.f32[2], d.f32lo[2]};
+  const df q_src{d.f32[3], d.f32lo[3]}, s0h{d.f32[4], d.f32lo[4]}, m_s0h = neg(s0h);
+  const df le0{d.f32[5], d.f32lo[5]}, lp0{d.f32[6], d.f32lo[6]}, lq0{d.f32[7], d.f32lo[7]};
+  const long long pos0 = start - halo + (long long)threadIdx.x * V;
+
+  df f[V][6];
+  bool lw[V], rw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const long long pos = pos0 + v;
+    lw[v] = WALLS && pos == 0;
+    rw[v] = WALLS && pos == N - 1;
+    long long lp = pos;
+    if (!WALLS) {
+      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+    } else {
+      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+    }
+    const double* src = in + off + lp;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) f[v][i] = to_df(src[i * plane]);
+  }
+
+  for (int k = 0; k < K; ++k) {
+    NodeS<df> m[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) node_state_s(f[v], c, m_s0h, m[v]);
+    df uL = shfl_up(m[V - 1].u), TL = shfl_up(m[V - 1].th);
+    df uR = shfl_down(m[0].u), TR = shfl_down(m[0].th);
+    if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].th; }
+    if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].th; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
+
+    df fs[V][6];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      df ul = v > 0 ? m[v - 1].u : uL, Tl = v > 0 ? m[v - 1].th : TL;
+      df ur = v < V - 1 ? m[v + 1].u : uR, Tr = v < V - 1 ? m[v + 1].th : TR;
+      if (lw[v]) { ul = neg(m[v].u); Tl = m[v].th; }
+      if (rw[v]) { ur = neg(m[v].u); Tr = m[v].th; }
+      node_collide_s(m[v], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[v], le0, lp0, lq0);
+    }
+    // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
+    df fpL = shfl_up(fs[V - 1][1]), gpL = shfl_up(fs[V - 1][4]);
+    df fmR = shfl_down(fs[0][2]), gmR = shfl_down(fs[0][5]);
+    if (lane == 31) { e_f[warp][0] = fs[V - 1][1]; e_f[warp][1] = fs[V - 1][4]; }
+    if (lane == 0) { e_f[warp][2] = fs[0][2]; e_f[warp][3] = fs[0][5]; }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      f[v][0] = fs[v][0];
+      f[v][3] = fs[v][3];
+      f[v][1] = lw[v] ? fs[v][2] : (v > 0 ? fs[v - 1][1] : fpL);
+      f[v][4] = lw[v] ? fs[v][5] : (v > 0 ? fs[v - 1][4] : gpL);
+      f[v][2] = rw[v] ? fs[v][1] : (v < V - 1 ? fs[v + 1][2] : fmR);
+      f[v][5] = rw[v] ? fs[v][4] : (v < V - 1 ? fs[v + 1][5] : gmR);
+    }
+  }
+
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int local = threadIdx.x * V + v;
+    const long long pos = pos0 + v;
+    if (local >= halo && local < halo + bout && pos < N) {
+      double* dst = out + off + pos;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) dst[i * plane] = to_double(f[v][i]);
+    }
+  }
+}
+
+template <int NT, int V>
+__global__ void __launch_bounds__(NT) step_tiles_df_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                           long long plane, const LatDev* __restrict__ lat,
+                                                           const int* __restrict__ tile_lat, int B, long long ntiles,
+                                                           int K, Consts<df> c) {
+  __shared__ df e_ut[NT / 32][4];
+  __shared__ df e_f[NT / 32][4];
+  const long long bout = NT * V - 4 * K;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int L = B > 1 ? tile_lat[tile] : 0;
+    const LatDev d = lat[L];
+    if (d.bc == 0) tile_body_df<NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+    else tile_body_df<NT, V, true>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+    __syncthreads();  // the next tile rewrites the edge buffers
+  }
+}
+
+template <int NT, int V>
+cudaError_t launch_df_nt_v(const double* in, double* out, long long plane, const LatDev* lat, const int* tile_lat,
+                           int B, long long ntiles, int K, const Consts<df>& c, cudaStream_t st, long long grid) {
+  step_tiles_df_kernel<NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, tile_lat, B, ntiles, K, c);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool valid_df_config(int K, int NT, int V) {
+  const bool nt_ok = NT == 128 || NT == 256 || NT == 512;
+  const bool v_ok = V == 1 || V == 2;
+  const bool k_ok = K == 1 || K == 2 || K == 4 || K == 8;
+  return nt_ok && v_ok && k_ok && NT * V - 4 * K >= 32;
+}
+
+cudaError_t launch_step_tiles_df(const double* in, double* out, long long plane, const LatDev* lat,
+                                 const int* tile_lat, int B, long long ntiles, int K, int NT, int V,
+                                 const Consts<df>& c, cudaStream_t st, long long grid_cap) {
+  if (ntiles <= 0) return cudaSuccess;
+  long long grid = ntiles;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
+#define DF_CASE(nt, v) \
+  if (NT == nt && V == v) return launch_df_nt_v<nt, v>(in, out, plane, lat, tile_lat, B, ntiles, K, c, st, grid);
+  DF_CASE(128, 1) DF_CASE(128, 2) DF_CASE(256, 1) DF_CASE(256, 2) DF_CASE(512, 1) DF_CASE(512, 2)
+#undef DF_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

@@ -33,11 +33,12 @@ LBM_BC_PERIODIC = 0
 LBM_BC_BOUNCEBACK = 1
 LBM_F64 = 0
 LBM_F32_SHIFTED = 1
+LBM_F64_DF = 2
 LBM_MODE_LAUNCH = 0
 LBM_MODE_PERSISTENT = 1
 LBM_MODE_PERSISTENT_GRAPH = 2
 MODES = {"launch": LBM_MODE_LAUNCH, "persistent": LBM_MODE_PERSISTENT, "graph": LBM_MODE_PERSISTENT_GRAPH}
-PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED}
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED, "f64df": LBM_F64_DF}
 
 
 class LbmError(RuntimeError):
@@ -118,6 +119,7 @@ def load_library(path: str = LIB_PATH):
             "lbm_diagnostics_noalloc": (i32, [vp, i64, d, P(lbm_phys), vp, vp, vp]),
             "lbm_set_mode": (i32, [vp, i32]),
             "lbm_debug_eval_f32": (i32, [vp, vp, i64, i32, vp]),
+            "lbm_debug_eval_df": (i32, [vp, vp, vp, i64, i32, vp]),
             "lbm_adjoint_forward": (i32, [vp, i64]),
             "lbm_adjoint_backward": (i32, [vp, vp, vp, vp, vp, vp]),
             "lbm_adjoint": (i32, [vp, i64, vp, vp, vp, vp, vp]),
