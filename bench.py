@@ -366,8 +366,10 @@ def run_adjoint(args, lbm, torch):
 
     B, N = args.adjoint_lattices, 65536
     out = {}
-    for prec, T in (("f32", args.adjoint_steps_f32), ("f64", args.adjoint_steps_f64)):
-        if prec not in args.precisions.split(","):
+    for prec, T in (("f32", args.adjoint_steps_f32), ("f64", args.adjoint_steps_f64),
+                    ("f64df", args.adjoint_steps_f64)):
+        base = "f64" if prec == "f64df" else prec  # the double-float leg runs with the FP64 one
+        if base not in args.precisions.split(","):
             continue
         rho, u, p = W.gaussian_bumps(B, N, 2369, W.reference_pressure())
         rho_t, u_t, p_t = W.gaussian_bumps(B, N, 2370, W.reference_pressure())

@@ -218,8 +218,9 @@ int lbm_adjoint(lbm_ctx *ctx, int64_t T, const double *rho_target, double *loss,
                 double *dL_du0, double *dL_drates);
 int lbm_adjoint_release(lbm_ctx *ctx);
 /* Reverse steps per launch of the backward sweep: 1, 2, 4 or 8 (0 selects the default: 4 for
- * LBM_F32_SHIFTED, where it halves the backward time against 1, and 1 for LBM_F64, whose arithmetic
- * bound makes the on-chip recomputation of inner states a net cost). Each
+ * LBM_F32_SHIFTED and LBM_F64_DF, where it halves the backward time against 1, and 1 for LBM_F64,
+ * whose arithmetic bound makes the on-chip recomputation of inner states a net cost). A LBM_F64_DF
+ * context runs its forward steps, the recomputation and the reverse steps in double-float. Each
  * segment is split into blocks of that many steps; the states at the block starts are recomputed
  * with launches of the step kernel, and one launch per block recomputes the block's inner states on
  * chip and runs its reverse steps (HBM traffic per node-step falls with the depth; the tile halo,

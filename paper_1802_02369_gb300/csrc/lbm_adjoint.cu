@@ -10,12 +10,16 @@
 //   3. transpose of the equation of state (eq. gaz-parfait) and of m = M f (eq. M-d1q3q3).
 // The dependency radius is 2 (as in the forward step). A launch runs K such steps on a tile after
 // recomputing the K forward states it needs from the one state at the start of the block.
+#include <type_traits>
+
+#include "lbm_df.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
-// Lanes: a thread holds W consecutive nodes in one lane value X (W = 1: X = double or float; W = 2:
-// X = float2, two nodes on Blackwell's paired FP32 instructions).
+// Lanes: a thread holds W consecutive nodes in one lane value X (W = 1: X = double, float, or df,
+// the double-float of lbm_df.cuh over FP64 storage; W = 2: X = float2, two nodes on Blackwell's paired
+// FP32 instructions). R is the storage type.
 template <typename X>
 struct Lane {
   using R = X;
@@ -26,32 +30,45 @@ struct Lane<float2> {
   using R = float;
   static constexpr int W = 2;
 };
+template <>
+struct Lane<df> {
+  using R = double;
+  static constexpr int W = 1;
+};
 __device__ __forceinline__ double lget(double x, int) { return x; }
 __device__ __forceinline__ float lget(float x, int) { return x; }
 __device__ __forceinline__ float lget(float2 x, int j) { return j ? x.y : x.x; }
+__device__ __forceinline__ double lget(df x, int) { return to_double(x); }
 __device__ __forceinline__ void lset(double& x, int, double v) { x = v; }
 __device__ __forceinline__ void lset(float& x, int, float v) { x = v; }
 __device__ __forceinline__ void lset(float2& x, int j, float v) {
   if (j) x.y = v;
   else x.x = v;
 }
+__device__ __forceinline__ void lset(df& x, int, double v) { x = to_df(v); }
 template <typename X>
 __device__ __forceinline__ X lit(double v) {
   if constexpr (Lane<X>::W == 2) return make_float2((float)v, (float)v);
+  else if constexpr (std::is_same<X, df>::value) return df_from_double_host(v);  // folded for constants
   else return X(v);
 }
 template <typename X>
 __device__ __forceinline__ X lit_r(typename Lane<X>::R v) {
   if constexpr (Lane<X>::W == 2) return make_float2(v, v);
+  else if constexpr (std::is_same<X, df>::value) return to_df(v);
   else return v;
 }
 // Per-lane select: lane j takes a where b[j], else keeps x.
 template <typename X>
 __device__ __forceinline__ X sel(const bool (&b)[Lane<X>::W], X a, X x) {
+  if constexpr (Lane<X>::W == 1) {
+    return b[0] ? a : x;
+  } else {
 #pragma unroll
-  for (int j = 0; j < Lane<X>::W; ++j)
-    if (b[j]) lset(x, j, lget(a, j));
-  return x;
+    for (int j = 0; j < Lane<X>::W; ++j)
+      if (b[j]) lset(x, j, lget(a, j));
+    return x;
+  }
 }
 
 // Shared-memory exchange buffers of one CTA of NT threads, one lane value per thread (W nodes), so a
@@ -547,6 +564,14 @@ static cudaError_t launch_block_lanes(const typename Lane<X>::R* f0, const typen
   adjoint_block_kernel<X, NT><<<(unsigned)ntiles, NT, use, st>>>(f0, a_next, a_out, plane, lat, B, ntiles, K, c,
                                                                  grad_tile);
   return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_block_df(const double* f0, const double* a_next, double* a_out, long long plane,
+                                    const LatDev* lat, int B, long long ntiles, int K, const Consts<df>& c,
+                                    double* grad_tile, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (K < 1 || K > kAdjointMaxK) return cudaErrorInvalidValue;
+  return launch_block_lanes<df>(f0, a_next, a_out, plane, lat, B, ntiles, K, c, grad_tile, st);
 }
 
 template <typename R>

@@ -609,7 +609,7 @@ int do_create(lbm_ctx** out, int B, const int64_t* N, double lambda, const lbm_r
   c->Ntot = tot;
   const bool f32 = precision == LBM_F32_SHIFTED;
   c->K = precision == LBM_F64 ? 1 : 4;
-  c->adj_K = f32 ? 4 : 1;  // measured fastest (FP64 is bound by its arithmetic)
+  c->adj_K = precision == LBM_F64 ? 1 : 4;  // measured fastest (FP64 is bound by its arithmetic)
   c->NT = precision == LBM_F64 ? 512 : 256;
   c->V = f32 ? 2 : 1;
   rebuild_tables(c);
@@ -1128,7 +1128,7 @@ int adjoint_forward_impl(lbm_ctx* c, long long T) {
   for (long long j = 0; j < nseg; ++j) {
     LBM_CK(c, cudaMemcpyAsync(c->ckpt[j], c->state[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
     const long long len = std::min(seg, T - j * seg);
-    rc = run_steps<R>(c, len);
+    rc = c->precision == LBM_F64_DF ? run_steps_df(c, len) : run_steps<R>(c, len);
     if (rc) { c->mode = save_mode; return rc; }
   }
   c->mode = save_mode;
@@ -1145,6 +1145,7 @@ int adjoint_forward_impl(lbm_ctx* c, long long T) {
 template <typename R>
 int adjoint_reverse(lbm_ctx* c, int* res) {
   const lbm::ConstSet<R> k = make_constset<R>(c->ph);
+  const Consts<lbm::df> kdf = make_consts<lbm::df>(c->ph);
   const int KA = c->adj_K;
   for (int K = 1; K <= lbm::kAdjointMaxK; ++K)
     LBM_CK(c, cudaMemsetAsync(c->d_gtile[K - 1], 0, sizeof(double) * 2 * c->adj_ntiles[K - 1], c->stream));
@@ -1155,17 +1156,38 @@ int adjoint_reverse(lbm_ctx* c, int* res) {
     std::vector<const R*> st(nb);
     st[0] = (const R*)c->ckpt[j];
     for (long long b = 1; b < nb; ++b) {
-      cudaError_t e = lbm::launch_step_tiles<R>(st[b - 1], (R*)c->stash[b - 1], c->Ntot, lat_for(c, KA),
-                                                tile_map_for(c, KA), c->B, c->ntiles_k[depth_index(KA)], KA, c->NT,
-                                                c->V, k, c->stream, 0);
+      cudaError_t e;
+      if constexpr (std::is_same<R, double>::value) {
+        if (c->precision == LBM_F64_DF) {
+          e = lbm::launch_step_tiles_df(st[b - 1], (double*)c->stash[b - 1], c->Ntot, lat_for(c, KA),
+                                        tile_map_for(c, KA), c->B, c->ntiles_k[depth_index(KA)], KA, c->NT, c->V,
+                                        kdf, c->stream, 0);
+          if (e != cudaSuccess) return cuda_fail(c, e, "adjoint recompute");
+          st[b] = (const R*)c->stash[b - 1];
+          continue;
+        }
+      }
+      e = lbm::launch_step_tiles<R>(st[b - 1], (R*)c->stash[b - 1], c->Ntot, lat_for(c, KA),
+                                    tile_map_for(c, KA), c->B, c->ntiles_k[depth_index(KA)], KA, c->NT,
+                                    c->V, k, c->stream, 0);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint recompute");
       st[b] = (const R*)c->stash[b - 1];
     }
     for (long long b = nb - 1; b >= 0; --b) {
       const int Kb = (int)std::min<long long>(KA, len - b * KA);
-      cudaError_t e = lbm::launch_adjoint_block<R>(st[b], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot,
-                                                   c->d_lat_adj + (size_t)(Kb - 1) * c->B, c->B,
-                                                   c->adj_ntiles[Kb - 1], Kb, k, c->d_gtile[Kb - 1], c->stream);
+      const LatDev* tab = c->d_lat_adj + (size_t)(Kb - 1) * c->B;
+      cudaError_t e;
+      if constexpr (std::is_same<R, double>::value) {
+        if (c->precision == LBM_F64_DF)
+          e = lbm::launch_adjoint_block_df(st[b], (const double*)c->adj_a[a], (double*)c->adj_a[1 - a], c->Ntot, tab,
+                                           c->B, c->adj_ntiles[Kb - 1], Kb, kdf, c->d_gtile[Kb - 1], c->stream);
+        else
+          e = lbm::launch_adjoint_block<R>(st[b], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot, tab, c->B,
+                                           c->adj_ntiles[Kb - 1], Kb, k, c->d_gtile[Kb - 1], c->stream);
+      } else {
+        e = lbm::launch_adjoint_block<R>(st[b], (const R*)c->adj_a[a], (R*)c->adj_a[1 - a], c->Ntot, tab, c->B,
+                                         c->adj_ntiles[Kb - 1], Kb, k, c->d_gtile[Kb - 1], c->stream);
+      }
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
       a = 1 - a;
     }
@@ -1268,7 +1290,7 @@ int lbm_adjoint_release(lbm_ctx* c) {
 
 int lbm_adjoint_set_config(lbm_ctx* c, int32_t steps_per_launch) {
   if (!c) return LBM_ERR_INVALID_ARG;
-  const int K = steps_per_launch > 0 ? steps_per_launch : (c->f64() ? 1 : 4);
+  const int K = steps_per_launch > 0 ? steps_per_launch : (c->precision == LBM_F64 ? 1 : 4);
   if (K != 1 && K != 2 && K != 4 && K != 8)
     return fail(c, LBM_ERR_INVALID_ARG, "adjoint_set_config: steps_per_launch must be 1, 2, 4 or 8");
   c->adj_K = K;

@@ -138,4 +138,9 @@ cudaError_t launch_step_tiles_df(const double* in, double* out, long long plane,
                                  const int* tile_lat, int B, long long ntiles, int K, int NT, int V,
                                  const Consts<df>& c, cudaStream_t st, long long grid_cap);
 
+// Adjoint block kernel on double-float lanes over FP64 storage (lbm_adjoint.cu).
+cudaError_t launch_adjoint_block_df(const double* f0, const double* a_next, double* a_out, long long plane,
+                                    const LatDev* lat, int B, long long ntiles, int K, const Consts<df>& c,
+                                    double* grad_tile, cudaStream_t st);
+
 }  // namespace lbm

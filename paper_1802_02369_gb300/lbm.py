@@ -391,7 +391,7 @@ class Lattice:
         self._check(self.lib.lbm_adjoint_release(self.ctx), "lbm_adjoint_release")
 
     def set_adjoint_config(self, steps_per_launch: int = 0):
-        """Reverse steps per launch of the backward sweep (1, 2, 4, 8; 0 = the default: 4 in FP32, 1 in FP64)."""
+        """Reverse steps per launch of the backward sweep (1, 2, 4, 8; 0 = the default: 1 in FP64, else 4)."""
         self._check(self.lib.lbm_adjoint_set_config(self.ctx, int(steps_per_launch)), "lbm_adjoint_set_config")
 
     def get_adjoint_config(self) -> int:

@@ -279,3 +279,24 @@ def test_adjoint_depths_agree(lbm, T):
         for i in (1, 2, 3):  # FP32: the inner states are recomputed in scalar lanes
             c, d = res["f32", K][i], res["f64", 1][i]
             assert np.abs(c - d).max() <= 2e-4 * np.abs(d).max(), (K, i)
+
+
+def test_double_float_adjoint_matches_fp64(lbm):
+    """A double-float context (LBM_F64_DF) runs its forward steps and the adjoint's recomputation and
+    reverse steps in double-float: the gradients agree with the native FP64 adjoint to FP64-class
+    accuracy, for every depth."""
+    lengths, bc, s_e, data, targets = _case()
+    init = [np.concatenate([d[k] for d in data]) for k in range(3)]
+    res = {}
+    for prec, K in (("f64", 1), ("f64df", 1), ("f64df", 4), ("f64df", 8)):
+        lat = lbm.Lattice(lengths, s_e=s_e, bc=bc, precision=prec)
+        lat.set_adjoint_config(K)
+        lat.set_state_entropy(*init)
+        res[prec, K] = lat.adjoint(50, np.concatenate(targets))
+        lat.close()
+    ref = res["f64", 1]
+    for key in (("f64df", 1), ("f64df", 4), ("f64df", 8)):
+        got = res[key]
+        assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0])
+        for i in (1, 2, 3):
+            assert np.abs(got[i] - ref[i]).max() <= 1e-10 * np.abs(ref[i]).max(), (key, i)
