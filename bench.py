@@ -263,9 +263,10 @@ def run_sweep(args, lbm, torch):
     """Precision and scale sweep: 64 lattices of 2^20 nodes, steepening wave of amplitude 0.2, lattice b
     with s_e = (1.2, 1.6, 1.9)[b mod 3], FP32 shifted populations and FP64, autotuned. Reported per
     precision: GLUPS over the timed steps, the per-step drift of the mass and momentum sums over the
-    first 100 steps, |sum(t) - sum(0)| / (t sum rho(0)), and the lattices flagged at the end (the
-    scheme is linearly unstable at |u| = 0.2: every lattice blows up from rounding noise within a few
-    hundred steps; the accuracy against the oracle is a parity test, not a bench figure)."""
+    first 20 steps, |sum(t) - sum(0)| / (t sum rho(0)), and the lattices flagged at the end (the
+    scheme is linearly unstable at |u| = 0.2: every lattice blows up from rounding noise, within about
+    a hundred steps in FP32 and a few hundred in FP64; the accuracy against the oracle is a parity
+    test, not a bench figure)."""
     from paper_1802_02369_gb300 import workloads as W
 
     B, N = 64, 1 << 20
@@ -280,9 +281,9 @@ def run_sweep(args, lbm, torch):
         k, nt, v = lat.autotune(1)
         lat.set_state(*fields)
         s0, _, _ = lat.diagnostics()
-        lat.step(100)
+        lat.step(20)
         s1, _, _ = lat.diagnostics()
-        drift = np.abs(s1[:, :2] - s0[:, :2]).max(axis=0) / (100 * s0[:, 0].max())
+        drift = np.abs(s1[:, :2] - s0[:, :2]).max(axis=0) / (20 * s0[:, 0].max())
         steps = (steps // k) * k
         lat.set_state(*fields)
         ms = time_device(lat, torch, steps, 3 * k, None, 1)
