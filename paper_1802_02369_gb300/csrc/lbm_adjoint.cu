@@ -10,6 +10,7 @@
 //   3. transpose of the equation of state (eq. gaz-parfait) and of m = M f (eq. M-d1q3q3).
 // The dependency radius is 2 (as in the forward step). A launch runs K such steps on a tile after
 // recomputing the K forward states it needs from the one state at the start of the block.
+#include <atomic>
 #include <type_traits>
 
 #include "lbm_df.cuh"
@@ -553,12 +554,16 @@ static cudaError_t launch_block_lanes(const typename Lane<X>::R* f0, const typen
   using R = typename Lane<X>::R;
   constexpr int NT = kAdjointThreads / Lane<X>::W;
   const size_t dyn = (size_t)kAdjointMaxK * 6 * kAdjointThreads * sizeof(R);
-  static bool attr_set = false;  // once per lane type and process (the limit is per function)
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_block_kernel<X, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dyn);
+  // The shared-memory limit is an attribute of the function on each device: set it once per device.
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ULL << (dev & 63);
+  if (dev >= 64 || !(attr_set.load() & bit)) {
+    e = cudaFuncSetAttribute(adjoint_block_kernel<X, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev < 64) attr_set.fetch_or(bit);
   }
   const size_t use = (size_t)K * 6 * kAdjointThreads * sizeof(R);
   adjoint_block_kernel<X, NT><<<(unsigned)ntiles, NT, use, st>>>(f0, a_next, a_out, plane, lat, B, ntiles, K, c,
