@@ -643,8 +643,11 @@ def run_ours(args, rank: int, world: int, local: int, dist):
         O.build()
         cores = os.cpu_count() or 1
         g, st, dt = cpu_oracle_rate(N_SAMPLE, 15.0, cores)
+        g1, st1, dt1 = cpu_oracle_rate(1 << 18, 4.0, 1)
         cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first 2^22 nodes of the workload (periodic), {st} steps, {dt:.1f} s, FP64"}
+               "sample": f"first 2^22 nodes of the workload (periodic), {st} steps, {dt:.1f} s, FP64",
+               "single_core": {"value": g1, "unit": UNIT, "cores": 1,
+                               "sample": f"first 2^18 nodes (periodic), {st1} steps, {dt1:.1f} s, FP64"}}
 
     props = torch.cuda.get_device_properties(local)
     sm_clock_mhz = clocks.get("sm_max_mhz") or 2070.0
