@@ -413,13 +413,13 @@ def run_adjoint(args, lbm, torch):
 FD_NU = 1.0 / S_E - 0.5
 FD_DT = 1.0
 FD_BYTES_PER_NODE = {"f32": 24, "f64": 48}
-# Executed arithmetic per computed node-step of the finite-difference kernel (CUDA's log1p, expm1 and
-# reciprocals included), from ncu instruction counts of one launch at N = 2^23 (2 FMA + ADD + MUL over
-# the tiles' node-steps, halo included): FP64 at (4, 256, 1) 2 x 1,835,804,672 DFMA + 762,032,128 DADD
-# + 762,032,128 DMUL over 33,826 x 256 x 4 node-steps = 150.0; FP32 at (8, 256, 2) 2 x 2,216,820,736
-# FFMA + 1,177,686,016 FADD + 1,662,615,552 FMUL over 16,913 x 512 x 8 = 105.0. Per output node-update
-# this is multiplied by the tile's computed / stored nodes, NT V / (NT V - 2K).
-FD_FLOPS_PER_COMPUTED = {"f64": 5195673600 / 34637824, "f32": 7273943040 / 69275648}
+# Arithmetic per computed node-step of the finite-difference kernel (halo included). FP64: executed, from
+# ncu at N = 2^23, (4, 256, 1): (2 x 1,766,529,024 DFMA + 831,307,776 DADD + 831,307,776 DMUL) over
+# 33,826 x 256 x 4 node-steps = 150.0 (CUDA's log1p, expm1 and reciprocals included). FP32 runs two nodes
+# per paired lane, which ncu's per-opcode counters do not split out; counted from the source (fma = 2):
+# 63 for the nodal quantities (series log1p 22 and expm1 17 included) + 37 for the update = 100. Per
+# output node-update this is multiplied by the tile's computed / stored nodes, NT V / (NT V - 2K).
+FD_FLOPS_PER_COMPUTED = {"f64": 5195673600 / 34637824, "f32": 100.0}
 
 
 def run_fd(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
