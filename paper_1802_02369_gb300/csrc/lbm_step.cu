@@ -419,7 +419,7 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 }
 
 template <typename R, int NT, int V>
-__global__ void __launch_bounds__(NT) persistent_kernel(R* buf0, R* buf1, long long plane,
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 8 : 0) persistent_kernel(R* buf0, R* buf1, long long plane,
                                                         const LatDev* __restrict__ lat,
                                                         const int* __restrict__ tile_lat, int B, long long ntiles,
                                                         int K, long long nblocks, PersistentCtl ctl,
