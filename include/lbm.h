@@ -17,7 +17,9 @@
  *  - Pointers to per-node arrays may be host or device pointers (told apart with
  *    cudaPointerGetAttributes). Host arrays are staged through a device buffer and the call
  *    synchronises the stream before returning; device arrays are used in place and the call only
- *    enqueues work on the context's stream (except where stated).
+ *    enqueues work on the context's stream (except where stated). lbm_set_state,
+ *    lbm_set_state_entropy and lbm_moments read or write page-locked (pinned) host arrays in place
+ *    from their kernels, over the CPU-GPU link, without the staging copy; they still synchronise.
  *  - All GPU work is enqueued on the stream given at creation (NULL = legacy default stream).
  *  - Ownership: the library owns the context and its device state; the caller owns every array
  *    it passes. Device memory is obtained through the allocator installed with

@@ -147,6 +147,17 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked (pinned) host memory, which kernels can read and write in place
+// over the CPU-GPU link (on GB300 the NVLink-C2C link to Grace); nullptr for pageable memory.
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Small kernels.
 
@@ -743,7 +754,14 @@ int set_state_impl(lbm_ctx* c, const double* rho, const double* u, const double*
   const bool host = !is_device_ptr(rho);
   if (host != !is_device_ptr(u) || host != !is_device_ptr(x))
     return fail(c, LBM_ERR_INVALID_ARG, "set_state: mix of host and device arrays");
-  if (host) {
+  const void *mr = host ? mapped_host_ptr(rho) : nullptr, *mu = host ? mapped_host_ptr(u) : nullptr;
+  const void* mx = host ? mapped_host_ptr(x) : nullptr;
+  if (host && mr && mu && mx) {
+    // Pinned host arrays: the initialisation kernel reads them in place (no staging copy).
+    dr = (const double*)mr;
+    du = (const double*)mu;
+    dx = (const double*)mx;
+  } else if (host) {
     int rc = ensure_stage(c, 3 * sizeof(double) * n);
     if (rc) return rc;
     LBM_CK(c, cudaMemcpyAsync(c->d_stage, rho, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
@@ -854,14 +872,22 @@ int lbm_moments(lbm_ctx* c, double* rho, double* J, double* zeta, double* e, dou
   if (host < 0) return LBM_OK;
   const long long n = c->Ntot;
   double* dst[6];
+  bool in_place = false;  // pinned host outputs: the kernel writes them directly
   if (host) {
+    in_place = true;
+    for (int i = 0; i < 6; ++i) {
+      dst[i] = outs[i] ? (double*)mapped_host_ptr(outs[i]) : nullptr;
+      if (outs[i] && !dst[i]) in_place = false;
+    }
+  }
+  if (host && !in_place) {
     int cnt = 0;
     for (double* p : outs) cnt += p != nullptr;
     int rc = ensure_stage(c, sizeof(double) * n * cnt);
     if (rc) return rc;
     int k = 0;
     for (int i = 0; i < 6; ++i) dst[i] = outs[i] ? c->d_stage + (k++) * n : nullptr;
-  } else {
+  } else if (!host) {
     for (int i = 0; i < 6; ++i) dst[i] = outs[i];
   }
   const InitArgs a = init_args(c);
@@ -873,8 +899,9 @@ int lbm_moments(lbm_ctx* c, double* rho, double* J, double* zeta, double* e, dou
                                                                       a, dst[0], dst[1], dst[2], dst[3], dst[4], dst[5]);
   LBM_CK(c, cudaGetLastError());
   if (host) {
-    for (int i = 0; i < 6; ++i)
-      if (outs[i]) LBM_CK(c, cudaMemcpyAsync(outs[i], dst[i], sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (!in_place)
+      for (int i = 0; i < 6; ++i)
+        if (outs[i]) LBM_CK(c, cudaMemcpyAsync(outs[i], dst[i], sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
   }
   return LBM_OK;

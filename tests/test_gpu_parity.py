@@ -230,6 +230,33 @@ def test_host_and_device_inputs_agree(lbm):
     b.close()
 
 
+def test_pinned_host_arrays_are_used_in_place(lbm):
+    """Page-locked host inputs and outputs (read and written by the kernels over the CPU-GPU link)
+    give bitwise the results of device arrays and of pageable host arrays."""
+    import torch
+
+    rho, u, p = smooth_data(5000, seed=4)
+    pinned = [torch.from_numpy(x).pin_memory() for x in (rho, u, p)]
+    outs = {}
+    for name, fields in (("pinned", pinned), ("device", [x.cuda() for x in pinned]), ("pageable", [rho, u, p])):
+        for prec in ("f64", "f32"):
+            lat = lbm.Lattice(5000, s_e=1.4, precision=prec)
+            lat.set_state(*fields)
+            lat.step(40)
+            if name == "pinned":
+                o = [torch.empty(5000, dtype=torch.float64).pin_memory() for _ in range(6)]
+                lat.moments(out=o)
+                outs[name, prec] = [x.numpy().copy() for x in o]
+            else:
+                outs[name, prec] = [np.asarray(x.cpu() if hasattr(x, "cpu") else x) for x in
+                                    lat.moments(device=(name == "device"))]
+            lat.close()
+    for prec in ("f64", "f32"):
+        for k in range(6):
+            assert np.array_equal(outs["pinned", prec][k], outs["device", prec][k])
+            assert np.array_equal(outs["pinned", prec][k], outs["pageable", prec][k])
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_checkpoint_resume_is_bitwise(lbm, tmp_path, precision):
     rho, u, p = smooth_data(5000, seed=9, amp=0.05)
@@ -460,3 +487,36 @@ def test_riemann_batch_full_size_sampled(O, lbm):
             assert flags[b] == 0 and np.mean(np.abs(got - O.moments(phb, fd)[:, 0])) <= 1e-4, b
         else:
             assert flags[b] != 0, b
+
+
+def test_precision_sweep_full_size_sampled(O, lbm):
+    """The precision and scale sweep at full size (64 lattices of 2^20 nodes, amplitude 0.2, lattice b
+    with s_e = (1.2, 1.6, 1.9)[b mod 3], autotuned as in the benchmark), after 20 steps (before the
+    linear instability amplifies rounding past the tolerances): windows around sampled nodes of four
+    lattices against the oracle on extended periodic windows (a node after T steps depends on the
+    initial data within 2T nodes)."""
+    import torch
+
+    ph = O.default_phys()
+    N, B, T = 1 << 20, 64, 20
+    s_vals = np.array([1.2, 1.6, 1.9])
+    s_e = s_vals[np.arange(B) % 3]
+    rho, u, p = W.steepening_wave(N, 0.2, ph.p0)
+    fields = [torch.from_numpy(np.tile(x, B)).cuda() for x in (rho, u, p)]
+    for precision, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        lat = lbm.Lattice(np.full(B, N), s_e=s_e, precision=precision)
+        lat.set_state(*fields)
+        lat.autotune(1)
+        lat.set_state(*fields)
+        lat.step(T)
+        g = [x.cpu().numpy() for x in lat.moments(device=True)]
+        lat.close()
+        for b in (0, 1, 2, 63):
+            for c in (0, N // 2 + 7, N - 1):
+                idx = (np.arange(c - 2 * T - 32, c + 2 * T + 32)) % N
+                fd = O.init(ph, rho[idx], u[idx], p=p[idx])
+                ref = O.moments(ph, O.run(ph, O.coupled_rates(s_e[b]), fd, T))[2 * T:2 * T + 64]
+                got = [x[b * N + idx[2 * T:2 * T + 64]] for x in g]
+                assert rel_err(got, ref, scales()).max() <= tol, (precision, b, c)
+    del fields
+    torch.cuda.empty_cache()
