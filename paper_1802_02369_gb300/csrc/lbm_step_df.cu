@@ -1,5 +1,6 @@
 // Fused collide-stream step of the D1Q3Q3 scheme (section 8, steps (i)-(viii)) with FP64 storage and
-// double-float arithmetic on the FP32 pipes (precision LBM_F64_DF).
+// double-float arithmetic on the FP32 pipes (precision LBM_F64_DF); one node per thread on scalar df
+// lanes, two or four on paired df2 lanes.
 //
 // The same temporally blocked tile update as the step kernels of lbm_step.cu (tiles of NT*V nodes,
 // thread t holding nodes tV .. tV+V-1, K steps on chip, 2K halo nodes recomputed per side), with every
@@ -7,6 +8,8 @@
 // loaded, the dimensionless node update of lbm_internal.cuh runs on df lanes, and the populations are
 // summed back to FP64 when the tile is stored. Neighbour values cross threads by two shuffles (hi, lo)
 // and warps through shared memory.
+#include <cstddef>
+
 #include "lbm_df.cuh"
 #include "lbm_internal.cuh"
 
@@ -108,6 +111,135 @@ __device__ __forceinline__ void tile_body_df(const double* __restrict__ in, doub
   }
 }
 
+// The same tile update with two nodes per df2 lane (V = 2 or 4 nodes per thread), so that the
+// double-float arithmetic runs on Blackwell's paired FP32 instructions. Lane l of a thread holds nodes
+// 2l (x) and 2l + 1 (y). Every lane of a df2 operation is the FP32 operation sequence of the scalar df
+// one, so the states equal those of the one-node-per-thread kernel bit for bit.
+template <int NT, int V, bool WALLS>
+__device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, double* __restrict__ out,
+                                              long long plane, const LatDev& d, long long start, int K,
+                                              const Consts<df2>& c, df (*e_ut)[4], df (*e_f)[4]) {
+  constexpr int NW = NT / 32, NL = V / 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int halo = 2 * K;
+  const int bout = NT * V - 2 * halo;
+  const long long off = d.offset, N = d.n;
+  const auto par = [&](int i) { return df2{make_float2(d.f32[i], d.f32[i]), make_float2(d.f32lo[i], d.f32lo[i])}; };
+  const df2 s_e = par(0), s_psi = par(1), s_eps = par(2), q_src = par(3), s0h = par(4);
+  const df2 m_s0h{p_neg(s0h.hi), p_neg(s0h.lo)};
+  const df2 le0 = par(5), lp0 = par(6), lq0 = par(7);
+  const long long pos0 = start - halo + (long long)threadIdx.x * V;
+
+  df2 f[NL][6];
+  bool lw[V], rw[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const long long pos = pos0 + v;
+    lw[v] = WALLS && pos == 0;
+    rw[v] = WALLS && pos == N - 1;
+    long long lp = pos;
+    if (!WALLS) {
+      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+    } else {
+      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+    }
+    const double* src = in + off + lp;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) df2_set(f[v >> 1][i], v & 1, to_df(src[i * plane]));
+  }
+
+  for (int k = 0; k < K; ++k) {
+    NodeS<df2> m[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) node_state_s(f[l], c, m_s0h, m[l]);
+    df uL = shfl_up(df2_get(m[NL - 1].u, 1)), TL = shfl_up(df2_get(m[NL - 1].th, 1));
+    df uR = shfl_down(df2_get(m[0].u, 0)), TR = shfl_down(df2_get(m[0].th, 0));
+    if (lane == 31) { e_ut[warp][0] = df2_get(m[NL - 1].u, 1); e_ut[warp][1] = df2_get(m[NL - 1].th, 1); }
+    if (lane == 0) { e_ut[warp][2] = df2_get(m[0].u, 0); e_ut[warp][3] = df2_get(m[0].th, 0); }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
+
+    df2 fs[NL][6];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const df ux = df2_get(m[l].u, 0), uy = df2_get(m[l].u, 1);
+      const df tx = df2_get(m[l].th, 0), ty = df2_get(m[l].th, 1);
+      df2 ul = df2_of(l > 0 ? df2_get(m[l - 1].u, 1) : uL, ux);
+      df2 Tl = df2_of(l > 0 ? df2_get(m[l - 1].th, 1) : TL, tx);
+      df2 ur = df2_of(uy, l < NL - 1 ? df2_get(m[l + 1].u, 0) : uR);
+      df2 Tr = df2_of(ty, l < NL - 1 ? df2_get(m[l + 1].th, 0) : TR);
+      if (lw[2 * l]) { df2_set(ul, 0, neg(ux)); df2_set(Tl, 0, tx); }
+      if (lw[2 * l + 1]) { df2_set(ul, 1, neg(uy)); df2_set(Tl, 1, ty); }
+      if (rw[2 * l]) { df2_set(ur, 0, neg(ux)); df2_set(Tr, 0, tx); }
+      if (rw[2 * l + 1]) { df2_set(ur, 1, neg(uy)); df2_set(Tr, 1, ty); }
+      node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l], le0, lp0, lq0);
+    }
+    // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
+    df fpL = shfl_up(df2_get(fs[NL - 1][1], 1)), gpL = shfl_up(df2_get(fs[NL - 1][4], 1));
+    df fmR = shfl_down(df2_get(fs[0][2], 0)), gmR = shfl_down(df2_get(fs[0][5], 0));
+    if (lane == 31) { e_f[warp][0] = df2_get(fs[NL - 1][1], 1); e_f[warp][1] = df2_get(fs[NL - 1][4], 1); }
+    if (lane == 0) { e_f[warp][2] = df2_get(fs[0][2], 0); e_f[warp][3] = df2_get(fs[0][5], 0); }
+    __syncthreads();
+    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      f[l][0] = fs[l][0];
+      f[l][3] = fs[l][3];
+      // f+, g+ from the left node; f-, g- from the right node; walls reflect their own.
+      const df fpx = l > 0 ? df2_get(fs[l - 1][1], 1) : fpL, gpx = l > 0 ? df2_get(fs[l - 1][4], 1) : gpL;
+      const df fmy = l < NL - 1 ? df2_get(fs[l + 1][2], 0) : fmR, gmy = l < NL - 1 ? df2_get(fs[l + 1][5], 0) : gmR;
+      f[l][1] = df2_of(lw[2 * l] ? df2_get(fs[l][2], 0) : fpx, lw[2 * l + 1] ? df2_get(fs[l][2], 1) : df2_get(fs[l][1], 0));
+      f[l][4] = df2_of(lw[2 * l] ? df2_get(fs[l][5], 0) : gpx, lw[2 * l + 1] ? df2_get(fs[l][5], 1) : df2_get(fs[l][4], 0));
+      f[l][2] = df2_of(rw[2 * l] ? df2_get(fs[l][1], 0) : df2_get(fs[l][2], 1), rw[2 * l + 1] ? df2_get(fs[l][1], 1) : fmy);
+      f[l][5] = df2_of(rw[2 * l] ? df2_get(fs[l][4], 0) : df2_get(fs[l][5], 1), rw[2 * l + 1] ? df2_get(fs[l][4], 1) : gmy);
+    }
+  }
+
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int local = threadIdx.x * V + v;
+    const long long pos = pos0 + v;
+    if (local >= halo && local < halo + bout && pos < N) {
+      double* dst = out + off + pos;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) dst[i * plane] = to_double(df2_get(f[v >> 1][i], v & 1));
+    }
+  }
+}
+
+// Consts<df2> from Consts<df>: every double-float field on both lanes.
+Consts<df2> pair_consts(const Consts<df>& c) {
+  constexpr size_t n = offsetof(Consts<df>, eq_mode) / sizeof(df);
+  static_assert(offsetof(Consts<df2>, eq_mode) == n * sizeof(df2), "Consts layout");
+  Consts<df2> p;
+  const df* s = reinterpret_cast<const df*>(&c);
+  df2* t = reinterpret_cast<df2*>(&p);
+  for (size_t i = 0; i < n; ++i) t[i] = df2{make_float2(s[i].hi, s[i].hi), make_float2(s[i].lo, s[i].lo)};
+  p.eq_mode = c.eq_mode;
+  p.source_on = c.source_on;
+  return p;
+}
+
+template <int NT, int V>
+__global__ void __launch_bounds__(NT) step_tiles_df2_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                            long long plane, const LatDev* __restrict__ lat,
+                                                            const int* __restrict__ tile_lat, int B, long long ntiles,
+                                                            int K, Consts<df2> c) {
+  __shared__ df e_ut[NT / 32][4];
+  __shared__ df e_f[NT / 32][4];
+  const long long bout = NT * V - 4 * K;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int L = B > 1 ? tile_lat[tile] : 0;
+    const LatDev d = lat[L];
+    if (d.bc == 0) tile_body_df2<NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+    else tile_body_df2<NT, V, true>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+    __syncthreads();  // the next tile rewrites the edge buffers
+  }
+}
+
 template <int NT, int V>
 __global__ void __launch_bounds__(NT) step_tiles_df_kernel(const double* __restrict__ in, double* __restrict__ out,
                                                            long long plane, const LatDev* __restrict__ lat,
@@ -128,7 +260,12 @@ __global__ void __launch_bounds__(NT) step_tiles_df_kernel(const double* __restr
 template <int NT, int V>
 cudaError_t launch_df_nt_v(const double* in, double* out, long long plane, const LatDev* lat, const int* tile_lat,
                            int B, long long ntiles, int K, const Consts<df>& c, cudaStream_t st, long long grid) {
-  step_tiles_df_kernel<NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, tile_lat, B, ntiles, K, c);
+  if constexpr (V == 1) {
+    step_tiles_df_kernel<NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, tile_lat, B, ntiles, K, c);
+  } else {
+    step_tiles_df2_kernel<NT, V><<<(unsigned)grid, NT, 0, st>>>(in, out, plane, lat, tile_lat, B, ntiles, K,
+                                                                pair_consts(c));
+  }
   return cudaGetLastError();
 }
 
@@ -136,7 +273,7 @@ cudaError_t launch_df_nt_v(const double* in, double* out, long long plane, const
 
 bool valid_df_config(int K, int NT, int V) {
   const bool nt_ok = NT == 128 || NT == 256 || NT == 512;
-  const bool v_ok = V == 1 || V == 2;
+  const bool v_ok = V == 1 || V == 2 || V == 4;
   const bool k_ok = K == 1 || K == 2 || K == 4 || K == 8;
   return nt_ok && v_ok && k_ok && NT * V - 4 * K >= 32;
 }
@@ -149,7 +286,8 @@ cudaError_t launch_step_tiles_df(const double* in, double* out, long long plane,
   if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
 #define DF_CASE(nt, v) \
   if (NT == nt && V == v) return launch_df_nt_v<nt, v>(in, out, plane, lat, tile_lat, B, ntiles, K, c, st, grid);
-  DF_CASE(128, 1) DF_CASE(128, 2) DF_CASE(256, 1) DF_CASE(256, 2) DF_CASE(512, 1) DF_CASE(512, 2)
+  DF_CASE(128, 1) DF_CASE(128, 2) DF_CASE(128, 4) DF_CASE(256, 1) DF_CASE(256, 2) DF_CASE(256, 4)
+  DF_CASE(512, 1) DF_CASE(512, 2) DF_CASE(512, 4)
 #undef DF_CASE
   return cudaErrorInvalidValue;
 }
