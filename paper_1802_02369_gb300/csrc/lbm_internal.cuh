@@ -131,16 +131,21 @@ __device__ __forceinline__ void log1p_reduce(float x, float& t, float& m) {
   m = (float)e;
 }
 
+// Every lane's value depends on that lane alone (the other lane of the pair only decides whether the
+// range reduction runs): a lane inside the series range reduces to t = x, m = 0, and a lane outside
+// the domain takes CUDA's function.
 __device__ __forceinline__ float2 m_log1p(float2 x) {
   if (fabsf(x.x) <= 0.3f && fabsf(x.y) <= 0.3f) return atanh2_series(x);
-  if (!(x.x > -1.0f && x.y > -1.0f && x.x < 3.0e38f && x.y < 3.0e38f))
-    return make_float2(log1pf(x.x), log1pf(x.y));  // outside the domain or non-finite
-  float2 t, m;
-  log1p_reduce(x.x, t.x, m.x);
-  log1p_reduce(x.y, t.y, m.y);
+  const bool okx = x.x > -1.0f && x.x < 3.0e38f, oky = x.y > -1.0f && x.y < 3.0e38f;
+  float2 t = make_float2(0.0f, 0.0f), m = make_float2(0.0f, 0.0f);
+  if (okx) log1p_reduce(x.x, t.x, m.x);
+  if (oky) log1p_reduce(x.y, t.y, m.y);
   const float2 a = atanh2_series(t);
   const float ln2_hi = 0.693145752f, ln2_lo = 1.42860677e-06f;  // ln 2 = hi + lo, hi with 17 bits
-  return __ffma2_rn(m, make_float2(ln2_hi, ln2_hi), __ffma2_rn(m, make_float2(ln2_lo, ln2_lo), a));
+  float2 r = __ffma2_rn(m, make_float2(ln2_hi, ln2_hi), __ffma2_rn(m, make_float2(ln2_lo, ln2_lo), a));
+  if (!okx) r.x = log1pf(x.x);  // outside the domain or non-finite
+  if (!oky) r.y = log1pf(x.y);
+  return r;
 }
 
 __device__ __forceinline__ float2 expm1_series(float2 x) {  // |x| <= 0.35
@@ -157,15 +162,21 @@ __device__ __forceinline__ float2 expm1_series(float2 x) {  // |x| <= 0.35
 
 __device__ __forceinline__ float2 m_expm1(float2 x) {
   if (fabsf(x.x) <= 0.35f && fabsf(x.y) <= 0.35f) return expm1_series(x);
-  if (!(fabsf(x.x) <= 80.0f && fabsf(x.y) <= 80.0f)) return make_float2(expm1f(x.x), expm1f(x.y));
-  const float kx = rintf(x.x * 1.44269504f), ky = rintf(x.y * 1.44269504f);  // k = round(x / ln 2)
+  // k = round(x / ln 2); 0 on a lane inside the series range (2^0 expm1(x) + 0 is its series value)
+  // and on a lane outside |x| <= 80 or non-finite, which takes CUDA's function.
+  const bool okx = fabsf(x.x) <= 80.0f, oky = fabsf(x.y) <= 80.0f;
+  const float kx = (okx && !(fabsf(x.x) <= 0.35f)) ? rintf(x.x * 1.44269504f) : 0.0f;
+  const float ky = (oky && !(fabsf(x.y) <= 0.35f)) ? rintf(x.y * 1.44269504f) : 0.0f;
   const float2 k = make_float2(kx, ky);
   const float ln2_hi = 0.693145752f, ln2_lo = 1.42860677e-06f;
   float2 r = __ffma2_rn(k, make_float2(-ln2_hi, -ln2_hi), x);
   r = __ffma2_rn(k, make_float2(-ln2_lo, -ln2_lo), r);
   const float2 e = expm1_series(r);
   const float2 two_k = make_float2(__int_as_float(((int)kx + 127) << 23), __int_as_float(((int)ky + 127) << 23));
-  return __ffma2_rn(two_k, e, __fadd2_rn(two_k, make_float2(-1.0f, -1.0f)));
+  float2 out = __ffma2_rn(two_k, e, __fadd2_rn(two_k, make_float2(-1.0f, -1.0f)));
+  if (!okx) out.x = expm1f(x.x);
+  if (!oky) out.y = expm1f(x.y);
+  return out;
 }
 
 // Moments and thermodynamic state of one node (or node pair) from its shifted populations
@@ -257,8 +268,22 @@ struct NodeS {
   X rho1, inv, u, sg, lnr, E, th;  // 1 + r, 1/(1 + r), u', sigma, log1p(r), expm1(x), theta
 };
 
-template <typename X>
-__device__ __forceinline__ void node_state_s(const X f[6], const Consts<X>& c, X m_s0h, NodeS<X>& m) {
+// log1p / expm1 by their series alone on paired lanes, clearing ok where a lane is outside the
+// series range (the value is then to be recomputed by m_log1p / m_expm1).
+__device__ __forceinline__ float2 log1p_series_checked(float2 x, bool& ok) {
+  ok = ok && fabsf(x.x) <= 0.3f && fabsf(x.y) <= 0.3f;
+  return atanh2_series(x);
+}
+__device__ __forceinline__ float2 expm1_series_checked(float2 x, bool& ok) {
+  ok = ok && fabsf(x.x) <= 0.35f && fabsf(x.y) <= 0.35f;
+  return expm1_series(x);
+}
+
+// CHECKED (paired lanes only): log1p and expm1 by their series without a branch; the return value is
+// false when some lane left the series ranges, and the caller then runs the unchecked form, whose
+// results agree on every lane inside the ranges.
+template <typename X, bool CHECKED = false>
+__device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X m_s0h, NodeS<X>& m) {
   // (ii) moments, eq. (M-d1q3q3), scaled.
   const X tf = ad(f[1], f[2]), tg = ad(f[4], f[5]);
   m.r = ad(tf, f[0]);
@@ -271,14 +296,21 @@ __device__ __forceinline__ void node_state_s(const X f[6], const Consts<X>& c, X
   m.rho1 = ad(c.one, m.r);
   if (c.eq_mode == 1) {  // the linear equilibria need no equation of state (and there is no source)
     m.inv = m.u = m.sg = m.lnr = m.E = m.th = X{};
-    return;
+    return true;
   }
   m.inv = m_rcp(m.rho1);
   m.u = ml(m.j, m.inv);
   m.sg = ml(fm(m.r, m_s0h, m.z), m.inv);
-  m.lnr = m_log1p(m.r);
-  m.E = m_expm1(ml(c.gamma, ad(m.lnr, m.sg)));
+  bool ok = true;
+  if constexpr (CHECKED) {
+    m.lnr = log1p_series_checked(m.r, ok);
+    m.E = expm1_series_checked(ml(c.gamma, ad(m.lnr, m.sg)), ok);
+  } else {
+    m.lnr = m_log1p(m.r);
+    m.E = m_expm1(ml(c.gamma, ad(m.lnr, m.sg)));
+  }
   m.th = ml(fm(c.kth, m.E, c.kth), m.inv);
+  return ok;
 }
 
 template <typename X>

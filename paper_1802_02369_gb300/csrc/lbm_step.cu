@@ -187,8 +187,10 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 }
 
 // The same tile update for FP32 with two nodes per float2 lane (V = 2 or 4 nodes per thread), so
-// that the node arithmetic runs on Blackwell's paired FP32 instructions. Lane l of a thread holds
-// nodes 2l (x) and 2l + 1 (y).
+// that the node arithmetic runs on Blackwell's paired FP32 instructions. With NL = V/2 lanes, lane l
+// of a thread holds nodes l (x) and l + NL (y): the left neighbours of lane l > 0 are then exactly
+// lane l - 1 and the right neighbours of lane l < NL - 1 exactly lane l + 1, so only the two outer
+// lanes assemble a neighbour pair from two registers.
 template <int NT, int V, bool CG, bool WALLS>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
@@ -206,6 +208,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   const float2 lq0 = make_float2(P.lin_q0, P.lin_q0);
   const long long pos0 = start - halo + (long long)threadIdx.x * V;
 
+  // Node v of the thread sits in lane v % NL, half v / NL.
   float2 f[NL][6];
   bool lw[V], rw[V];
 #pragma unroll
@@ -220,7 +223,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
 #pragma unroll
     for (int l = 0; l < NL; ++l)
 #pragma unroll
-      for (int i = 0; i < 6; ++i) f[l][i] = make_float2(fl[2 * l][i], fl[2 * l + 1][i]);
+      for (int i = 0; i < 6; ++i) f[l][i] = make_float2(fl[l][i], fl[l + NL][i]);
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -234,7 +237,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         const float x = ld_state<float, CG>(src + i * plane);
-        if (v & 1) f[v >> 1][i].y = x; else f[v >> 1][i].x = x;
+        if (v >= NL) f[v - NL][i].y = x; else f[v][i].x = x;
       }
     }
   }
@@ -242,7 +245,10 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   for (int k = 0; k < K; ++k) {
     NodeS<float2> m[NL];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) node_state_s(f[l], c, m_s0h, m[l]);
+    for (int l = 0; l < NL; ++l) {  // series first; a pair with a node outside their ranges is redone
+      if (!node_state_s<float2, true>(f[l], c, m_s0h, m[l])) node_state_s(f[l], c, m_s0h, m[l]);
+    }
+    // Node V - 1 is lane NL - 1, half y; node 0 is lane 0, half x.
     float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].th.y, 1);
     float uR = __shfl_down_sync(0xffffffffu, m[0].u.x, 1), TR = __shfl_down_sync(0xffffffffu, m[0].th.x, 1);
     if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].th.y; }
@@ -254,14 +260,14 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     float2 fs[NL][6];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-      float2 ul = make_float2(l > 0 ? m[l - 1].u.y : uL, m[l].u.x);
-      float2 Tl = make_float2(l > 0 ? m[l - 1].th.y : TL, m[l].th.x);
-      float2 ur = make_float2(m[l].u.y, l < NL - 1 ? m[l + 1].u.x : uR);
-      float2 Tr = make_float2(m[l].th.y, l < NL - 1 ? m[l + 1].th.x : TR);
-      if (lw[2 * l]) { ul.x = -m[l].u.x; Tl.x = m[l].th.x; }
-      if (lw[2 * l + 1]) { ul.y = -m[l].u.y; Tl.y = m[l].th.y; }
-      if (rw[2 * l]) { ur.x = -m[l].u.x; Tr.x = m[l].th.x; }
-      if (rw[2 * l + 1]) { ur.y = -m[l].u.y; Tr.y = m[l].th.y; }
+      float2 ul = l > 0 ? m[l - 1].u : make_float2(uL, m[NL - 1].u.x);
+      float2 Tl = l > 0 ? m[l - 1].th : make_float2(TL, m[NL - 1].th.x);
+      float2 ur = l < NL - 1 ? m[l + 1].u : make_float2(m[0].u.y, uR);
+      float2 Tr = l < NL - 1 ? m[l + 1].th : make_float2(m[0].th.y, TR);
+      if (lw[l]) { ul.x = -m[l].u.x; Tl.x = m[l].th.x; }
+      if (lw[l + NL]) { ul.y = -m[l].u.y; Tl.y = m[l].th.y; }
+      if (rw[l]) { ur.x = -m[l].u.x; Tr.x = m[l].th.x; }
+      if (rw[l + NL]) { ur.y = -m[l].u.y; Tr.y = m[l].th.y; }
       node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l], le0, lp0, lq0);
     }
     float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
@@ -273,15 +279,21 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
+      // f+, g+ from the left node; f-, g- from the right node; walls reflect their own.
+      float2 fp = l > 0 ? fs[l - 1][1] : make_float2(fpL, fs[NL - 1][1].x);
+      float2 gp = l > 0 ? fs[l - 1][4] : make_float2(gpL, fs[NL - 1][4].x);
+      float2 fm_ = l < NL - 1 ? fs[l + 1][2] : make_float2(fs[0][2].y, fmR);
+      float2 gm = l < NL - 1 ? fs[l + 1][5] : make_float2(fs[0][5].y, gmR);
+      if (lw[l]) { fp.x = fs[l][2].x; gp.x = fs[l][5].x; }
+      if (lw[l + NL]) { fp.y = fs[l][2].y; gp.y = fs[l][5].y; }
+      if (rw[l]) { fm_.x = fs[l][1].x; gm.x = fs[l][4].x; }
+      if (rw[l + NL]) { fm_.y = fs[l][1].y; gm.y = fs[l][4].y; }
       f[l][0] = fs[l][0];
       f[l][3] = fs[l][3];
-      // f+, g+ from the left node; f-, g- from the right node; walls reflect their own.
-      const float fpx = l > 0 ? fs[l - 1][1].y : fpL, gpx = l > 0 ? fs[l - 1][4].y : gpL;
-      const float fmy = l < NL - 1 ? fs[l + 1][2].x : fmR, gmy = l < NL - 1 ? fs[l + 1][5].x : gmR;
-      f[l][1] = make_float2(lw[2 * l] ? fs[l][2].x : fpx, lw[2 * l + 1] ? fs[l][2].y : fs[l][1].x);
-      f[l][4] = make_float2(lw[2 * l] ? fs[l][5].x : gpx, lw[2 * l + 1] ? fs[l][5].y : fs[l][4].x);
-      f[l][2] = make_float2(rw[2 * l] ? fs[l][1].x : fs[l][2].y, rw[2 * l + 1] ? fs[l][1].y : fmy);
-      f[l][5] = make_float2(rw[2 * l] ? fs[l][4].x : fs[l][5].y, rw[2 * l + 1] ? fs[l][4].y : gmy);
+      f[l][1] = fp;
+      f[l][4] = gp;
+      f[l][2] = fm_;
+      f[l][5] = gm;
     }
   }
 
@@ -290,7 +302,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
 #pragma unroll
     for (int v = 0; v < V; ++v)
 #pragma unroll
-      for (int i = 0; i < 6; ++i) fl[v][i] = (v & 1) ? f[v >> 1][i].y : f[v >> 1][i].x;
+      for (int i = 0; i < 6; ++i) fl[v][i] = v >= NL ? f[v - NL][i].y : f[v][i].x;
     staged_store<float, NT, V>(out, plane, off, N, start - halo, halo, bout, stage, fl);
     return;
   }
@@ -301,7 +313,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     if (local >= halo && local < halo + bout && pos < N) {
       float* dst = out + off + pos;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) dst[i * plane] = (v & 1) ? f[v >> 1][i].y : f[v >> 1][i].x;
+      for (int i = 0; i < 6; ++i) dst[i * plane] = v >= NL ? f[v - NL][i].y : f[v][i].x;
     }
   }
 }

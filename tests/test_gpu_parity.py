@@ -121,6 +121,38 @@ def test_shocks_fp32_l1(O, lbm):
         assert np.mean(np.abs(np.asarray(g[0]) - ref[:, 0])) <= 1e-4
 
 
+def test_fp32_paired_lane_layouts_agree(O, lbm):
+    """FP32 with two nodes per thread (one float2 lane: nodes 0, 1) and four (two lanes: nodes 0, 2 and
+    1, 3) pairs different nodes on a lane, so the two layouts only agree when every node gets the same
+    FP32 operations whatever its partner: bitwise equal states at bounce-back walls, at lattice joints
+    of a ragged batch, and with every other node outside the series ranges of log1p / expm1 (the pair
+    then takes the range-reduced forms). Also within the FP32 tolerance of the oracle."""
+    ph = O.default_phys()
+    bat = W.ragged_batch(9, 77, ph.p0, n_min=33, n_max=700)
+    rng = np.random.default_rng(31)
+    n = int(np.sum(bat.lengths))
+    rho = 1 + 0.02 * rng.standard_normal(n)
+    rho[::2] += 0.45
+    u = 0.02 * rng.standard_normal(n)
+    p = ph.p0 * rho ** 1.4
+    out = []
+    for cfg in ((4, 128, 2), (4, 128, 4), (4, 512, 4), (4, 256, 2)):
+        lat = lbm.Lattice(bat.lengths, s_e=bat.s_e, bc=bat.bc, precision="f32")
+        lat.set_config(*cfg)
+        lat.set_state(rho, u, p)
+        lat.step(12)
+        out.append((lat.populations(), np.stack(lat.moments(device=False), axis=1)))
+        lat.close()
+    for pop, _ in out[1:]:
+        assert np.array_equal(pop, out[0][0])
+    m = out[0][1]
+    for b in range(bat.lengths.size):
+        phb = O.default_phys(bc=int(bat.bc[b]))
+        lo, hi = bat.offsets[b], bat.offsets[b + 1]
+        ref = O.moments(phb, O.run(phb, O.coupled_rates(bat.s_e[b]), O.init(phb, rho[lo:hi], u[lo:hi], p=p[lo:hi]), 12))
+        assert rel_err(tuple(m[lo:hi].T), ref, scales()).max() <= 1e-5, b
+
+
 def test_batched_ragged_fp64(O, lbm):
     """Independent lattices of uneven lengths, rates and boundaries in one context."""
     rng = np.random.default_rng(1802)
