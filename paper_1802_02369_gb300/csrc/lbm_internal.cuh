@@ -86,11 +86,17 @@ __device__ __forceinline__ float2 ml(float2 a, float2 b) { return __fmul2_rn(a, 
 __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float2 fm(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// Reciprocals: FP32 uses the hardware approximation (at most 2 ulp in the normal range), FP64 the
-// correctly rounded reciprocal.
-__device__ __forceinline__ float m_rcp(float x) { return __fdividef(1.0f, x); }
+// Reciprocals: FP32 uses the hardware approximation, one MUFU operation (relative error about 2^-23;
+// subnormal inputs and results flush to zero, which the positive, order-one denominators of the node
+// update never reach), FP64 the correctly rounded reciprocal.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float m_rcp(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double m_rcp(double x) { return __drcp_rn(x); }
-__device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y)); }
+__device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
 
 // log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes they are
 // evaluated with textbook series in paired arithmetic:

@@ -1,6 +1,6 @@
 """The FP32 series used on paired lanes (log1p by the atanh series, expm1 by its Taylor series)
 against FP64 and against CUDA's log1pf / expm1f, on their whole ranges and across the switch to
-CUDA's functions."""
+CUDA's functions; the FP32 reciprocal against FP64."""
 import numpy as np
 import pytest
 
@@ -40,3 +40,18 @@ def test_paired_series_accuracy(fn_pair, fn_cuda, ref, lim):
     # On the series range the paired result stays within 4 ulp of CUDA's function.
     inr = np.abs(x32) <= lim
     assert (np.abs(pair - cuda)[inr] / ulp[inr]).max() <= 4.0
+
+
+def test_reciprocal_accuracy():
+    """The FP32 reciprocal of the node update (densities 1 + r, 2 + t, temperatures theta: positive and
+    of order one, here over 1e-6 .. 1e6) within 2 ulp of the exact reciprocal of its FP32 input."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(5)
+    x = np.concatenate([np.linspace(0.05, 4.0, 300001), 10.0 ** rng.uniform(-6, 6, 200000),
+                        [1.0, 2.0, 0.5, 1.5, np.nextafter(np.float32(1), np.float32(2))]]).astype(np.float32)
+    exact = 1.0 / x.astype(np.float64)
+    got = _eval(x, 4)
+    ulp = np.spacing(exact.astype(np.float32)).astype(np.float64)
+    assert (np.abs(got - exact) / ulp).max() <= 2.0
