@@ -101,10 +101,11 @@ __device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(rcp_appro
 // log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes they are
 // evaluated with textbook series in paired arithmetic:
 //  - log1p(x) = m ln 2 + 2 atanh(z), z = t / (2 + t), with t = x and m = 0 for |x| <= 0.3, else
-//    1 + x = 2^m (1 + t), 1 + t in [0.75, 1.5); 2 atanh(z) = 2 z (1 + w/3 + w^2/5 + ... + w^5/11),
-//    w = z^2, |z| <= 0.2 (first omitted term below 1e-9 relative);
+//    1 + x = 2^m (1 + t), 1 + t in [0.75, 1.5); 2 atanh(z) = 2 z (1 + w/3 + w^2/5 + ... + w^4/9),
+//    w = z^2 <= 0.04 (first omitted term w^5/11 below 1e-8 relative, a sixth of an FP32 ulp);
 //  - expm1(x) = 2^k expm1(r) + (2^k - 1), x = k ln 2 + r, |r| <= ln(2)/2 (k = 0 for |x| <= 0.35),
-//    expm1(r) = r + r^2 (1/2! + r/3! + ... + r^7/9!) (first omitted term below 1e-9 relative).
+//    expm1(r) = r + r^2 (1/2! + r/3! + ... + r^5/7!) (first omitted term r^8/8! below 2e-8 of
+//    expm1(r), a third of an FP32 ulp).
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
@@ -117,8 +118,7 @@ __device__ __forceinline__ float2 atanh2_series(float2 t) {  // 2 atanh(t / (2 +
   y = __ffma2_rn(y, __ffma2_rn(nd, y, make_float2(1.0f, 1.0f)), y);  // Newton step
   const float2 z = __fmul2_rn(t, y);
   const float2 w = __fmul2_rn(z, z);
-  float2 p = make_float2(1.0f / 11.0f, 1.0f / 11.0f);
-  p = __ffma2_rn(p, w, make_float2(1.0f / 9.0f, 1.0f / 9.0f));
+  float2 p = make_float2(1.0f / 9.0f, 1.0f / 9.0f);
   p = __ffma2_rn(p, w, make_float2(1.0f / 7.0f, 1.0f / 7.0f));
   p = __ffma2_rn(p, w, make_float2(1.0f / 5.0f, 1.0f / 5.0f));
   p = __ffma2_rn(p, w, make_float2(1.0f / 3.0f, 1.0f / 3.0f));
@@ -155,9 +155,7 @@ __device__ __forceinline__ float2 m_log1p(float2 x) {
 }
 
 __device__ __forceinline__ float2 expm1_series(float2 x) {  // |x| <= 0.35
-  float2 p = make_float2(1.0f / 362880.0f, 1.0f / 362880.0f);
-  p = __ffma2_rn(p, x, make_float2(1.0f / 40320.0f, 1.0f / 40320.0f));
-  p = __ffma2_rn(p, x, make_float2(1.0f / 5040.0f, 1.0f / 5040.0f));
+  float2 p = make_float2(1.0f / 5040.0f, 1.0f / 5040.0f);
   p = __ffma2_rn(p, x, make_float2(1.0f / 720.0f, 1.0f / 720.0f));
   p = __ffma2_rn(p, x, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
   p = __ffma2_rn(p, x, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
@@ -287,8 +285,9 @@ __device__ __forceinline__ float2 expm1_series_checked(float2 x, bool& ok) {
 
 // CHECKED (paired lanes only): log1p and expm1 by their series without a branch; the return value is
 // false when some lane left the series ranges, and the caller then runs the unchecked form, whose
-// results agree on every lane inside the ranges.
-template <typename X, bool CHECKED = false>
+// results agree on every lane inside the ranges. FULL: the caller guarantees the nonlinear equilibria
+// with the entropy source (eq_mode 0, source_on), so those tests compile away.
+template <typename X, bool CHECKED = false, bool FULL = false>
 __device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X m_s0h, NodeS<X>& m) {
   // (ii) moments, eq. (M-d1q3q3), scaled.
   const X tf = ad(f[1], f[2]), tg = ad(f[4], f[5]);
@@ -300,7 +299,7 @@ __device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X
   m.ep = fm(f[3], c.m_two, tg);
   // Equation of state, eq. (gaz-parfait).
   m.rho1 = ad(c.one, m.r);
-  if (c.eq_mode == 1) {  // the linear equilibria need no equation of state (and there is no source)
+  if (!FULL && c.eq_mode == 1) {  // the linear equilibria need no equation of state (and there is no source)
     m.inv = m.u = m.sg = m.lnr = m.E = m.th = X{};
     return true;
   }
@@ -319,14 +318,14 @@ __device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X
   return ok;
 }
 
-template <typename X>
+template <typename X, bool FULL = false>
 __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X thl, X thr, X s_e, X s_psi,
                                                X s_eps, X q_src, X s0h, const Consts<X>& c, X fs[6],
                                                X lin_e0 = X{}, X lin_p0 = X{}, X lin_q0 = X{}) {
   // (iv) equilibria (eqs. energie-equilibre, psi-equilibre, eq-energie-entropie-d1q3q3), or the
   // linear ones of eq. (equilibres-NS-linearise).
   X e_eq, ps_eq, ep_eq;
-  if (c.eq_mode == 1) {
+  if (!FULL && c.eq_mode == 1) {
     e_eq = fm(c.leZ, m.z, fm(c.leJ, m.j, fm(c.leR, m.r, lin_e0)));
     ps_eq = fm(c.lpZ, m.z, fm(c.lpJ, m.j, fm(c.lpR, m.r, lin_p0)));
     ep_eq = fm(c.lqZ, m.z, fm(c.lqJ, m.j, fm(c.lqR, m.r, lin_q0)));
@@ -342,7 +341,7 @@ __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X 
   const X eps = fm(s_eps, sb(ep_eq, m.ep), m.ep);
   // (vii) entropy production (eq. NS-rho-J-zeta), centred differences.
   X zs = m.z;
-  if (c.source_on) {
+  if (FULL || c.source_on) {
     const X du = sb(ur, ul), dth = sb(thr, thl);
     const X ith = m_rcp(m.th);
     const X A = fm(ml(dth, dth), ml(ith, c.inv_Pr), ml(du, du));

@@ -191,7 +191,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 // of a thread holds nodes l (x) and l + NL (y): the left neighbours of lane l > 0 are then exactly
 // lane l - 1 and the right neighbours of lane l < NL - 1 exactly lane l + 1, so only the two outer
 // lanes assemble a neighbour pair from two registers.
-template <int NT, int V, bool CG, bool WALLS>
+template <int NT, int V, bool CG, bool WALLS, bool FULL>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
                                                  float (*e_ut)[4], float (*e_f)[4], float* stage) {
@@ -246,7 +246,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     NodeS<float2> m[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {  // series first; a pair with a node outside their ranges is redone
-      if (!node_state_s<float2, true>(f[l], c, m_s0h, m[l])) node_state_s(f[l], c, m_s0h, m[l]);
+      if (!node_state_s<float2, true, FULL>(f[l], c, m_s0h, m[l])) node_state_s<float2, false, FULL>(f[l], c, m_s0h, m[l]);
     }
     // Node V - 1 is lane NL - 1, half y; node 0 is lane 0, half x.
     float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].th.y, 1);
@@ -268,7 +268,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
       if (lw[l + NL]) { ul.y = -m[l].u.y; Tl.y = m[l].th.y; }
       if (rw[l]) { ur.x = -m[l].u.x; Tr.x = m[l].th.x; }
       if (rw[l + NL]) { ur.y = -m[l].u.y; Tr.y = m[l].th.y; }
-      node_collide_s(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l], le0, lp0, lq0);
+      node_collide_s<float2, FULL>(m[l], ul, ur, Tl, Tr, s_e, s_psi, s_eps, q_src, s0h, c, fs[l], le0, lp0, lq0);
     }
     float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
     float fmR = __shfl_down_sync(0xffffffffu, fs[0][2].x, 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5].x, 1);
@@ -347,8 +347,15 @@ __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane
                                             R (*e_f)[4], R* stage = nullptr) {
   // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
   if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
-    if (d.bc == 0) tile_body_packed<NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
-    else tile_body_packed<NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    // The paper's scheme (nonlinear equilibria, entropy source) without per-node mode tests.
+    const bool full = c.eq_mode == 0 && c.source_on;
+    if (d.bc == 0) {
+      if (full) tile_body_packed<NT, V, CG, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+      else tile_body_packed<NT, V, CG, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    } else {
+      if (full) tile_body_packed<NT, V, CG, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+      else tile_body_packed<NT, V, CG, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    }
   } else {
     if (d.bc == 0) tile_body<R, NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
     else tile_body<R, NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
