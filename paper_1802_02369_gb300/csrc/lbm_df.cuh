@@ -266,6 +266,14 @@ __device__ __forceinline__ df2 m_expm1(df2 x) {
   return r;
 }
 
+template <>
+__device__ __forceinline__ df num<df>(double v) { return df{(float)v, (float)(v - (double)(float)v)}; }
+template <>
+__device__ __forceinline__ df2 num<df2>(double v) {
+  const df a = num<df>(v);
+  return df2{make_float2(a.hi, a.hi), make_float2(a.lo, a.lo)};
+}
+
 // Step kernel in double-float (lbm_step_df.cu): FP64 storage, tiles of NT*V nodes, K steps per launch.
 bool valid_df_config(int K, int NT, int V);
 cudaError_t launch_step_tiles_df(const double* in, double* out, long long plane, const LatDev* lat,

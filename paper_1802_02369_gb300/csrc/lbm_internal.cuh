@@ -287,18 +287,29 @@ __device__ __forceinline__ float2 expm1_series_checked(float2 x, bool& ok) {
 // false when some lane left the series ranges, and the caller then runs the unchecked form, whose
 // results agree on every lane inside the ranges. FULL: the caller guarantees the nonlinear equilibria
 // with the entropy source (eq_mode 0, source_on), so those tests compile away.
+// Numeric constants of the node update in the lane type X, as the compiler's literals (rounded as
+// the host rounds the Consts fields).
+template <typename X>
+__device__ __forceinline__ X num(double v);
+template <>
+__device__ __forceinline__ double num<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float num<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ float2 num<float2>(double v) { return make_float2((float)v, (float)v); }
+
 template <typename X, bool CHECKED = false, bool FULL = false>
 __device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X m_s0h, NodeS<X>& m) {
   // (ii) moments, eq. (M-d1q3q3), scaled.
   const X tf = ad(f[1], f[2]), tg = ad(f[4], f[5]);
   m.r = ad(tf, f[0]);
   m.j = sb(f[1], f[2]);
-  m.e = fm(f[0], c.m_two, tf);
+  m.e = fm(f[0], num<X>(-2.0), tf);
   m.z = ad(tg, f[3]);
   m.ps = sb(f[4], f[5]);
-  m.ep = fm(f[3], c.m_two, tg);
+  m.ep = fm(f[3], num<X>(-2.0), tg);
   // Equation of state, eq. (gaz-parfait).
-  m.rho1 = ad(c.one, m.r);
+  m.rho1 = ad(num<X>(1.0), m.r);
   if (!FULL && c.eq_mode == 1) {  // the linear equilibria need no equation of state (and there is no source)
     m.inv = m.u = m.sg = m.lnr = m.E = m.th = X{};
     return true;
@@ -331,7 +342,7 @@ __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X 
     ep_eq = fm(c.lqZ, m.z, fm(c.lqJ, m.j, fm(c.lqR, m.r, lin_q0)));
   } else {
     const X sp = ad(s0h, m.sg);
-    e_eq = fm(m.r, c.m_two, ml(c.three, fm(m.j, m.u, ml(c.kp, m.E))));
+    e_eq = fm(m.r, num<X>(-2.0), ml(num<X>(3.0), fm(m.j, m.u, ml(c.kp, m.E))));
     ps_eq = ml(ml(m.rho1, sp), m.u);
     ep_eq = fm(c.e_rs, m.sg, fm(e_eq, sp, ml(ad(m.rho1, m.rho1), fm(c.one_m_ig, m.lnr, m.sg))));
   }
@@ -349,16 +360,16 @@ __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X 
   }
   // (vi) back to populations.
   {
-    const X h = ml(fm(m.r, c.two, es), c.sixth);
-    fs[0] = ml(sb(m.r, es), c.third);
-    fs[1] = fm(m.j, c.half, h);
-    fs[2] = fm(m.j, c.m_half, h);
+    const X h = ml(fm(m.r, num<X>(2.0), es), num<X>(1.0 / 6.0));
+    fs[0] = ml(sb(m.r, es), num<X>(1.0 / 3.0));
+    fs[1] = fm(m.j, num<X>(0.5), h);
+    fs[2] = fm(m.j, num<X>(-0.5), h);
   }
   {
-    const X h = ml(fm(zs, c.two, eps), c.sixth);
-    fs[3] = ml(sb(zs, eps), c.third);
-    fs[4] = fm(pss, c.half, h);
-    fs[5] = fm(pss, c.m_half, h);
+    const X h = ml(fm(zs, num<X>(2.0), eps), num<X>(1.0 / 6.0));
+    fs[3] = ml(sb(zs, eps), num<X>(1.0 / 3.0));
+    fs[4] = fm(pss, num<X>(0.5), h);
+    fs[5] = fm(pss, num<X>(-0.5), h);
   }
 }
 
