@@ -118,7 +118,9 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);   /* time steps taken since the last
 
 /* Equilibrium initial state f_d = M^{-1} m_eq(rho, J = rho u, zeta = rho s) from per-node rho, u
  * and pressure p (the specific entropy s follows from eq. (gaz-parfait)). Arrays of
- * lbm_total_nodes() float64, host or device. Resets the step counter. */
+ * lbm_total_nodes() float64, host or device. Resets the step counter. Computed in FP64 and rounded
+ * once to the storage type; for LBM_F32_SHIFTED the logarithms and the exponential are evaluated in
+ * double-float (about 48 bits), so the stored floats are the FP64 ones but for rare one-ulp ties. */
 int lbm_set_state(lbm_ctx *ctx, const double *rho, const double *u, const double *p);
 /* Same from rho, u and the specific entropy s. */
 int lbm_set_state_entropy(lbm_ctx *ctx, const double *rho, const double *u, const double *s);

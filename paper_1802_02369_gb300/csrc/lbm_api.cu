@@ -174,10 +174,27 @@ struct InitArgs {
   double rho0, p0, gamma, cp, lam, e_r, cp_log, wf0, wf1;
   int eq_mode;
   double u0_lin, s0_lin, a1, b1, c02;
+  // Reciprocals for the initialisation: 1/rho0, 1/p0, 1/c_p, c_p/gamma, and the moment scales
+  // 1/(rho0 lambda^k), 1/(rho0 c_p lambda^k), k = 0, 1, 2 (a product instead of an FP64 division).
+  double inv_rho0, inv_p0, inv_cp, cp_over_gamma, inv_af[3], inv_ag[3];
 };
 
+// log1p and expm1 of the initialisation: FP64 for FP64 storage; for FP32 storage double-float on the
+// FP32 pipes (about 48 significant bits, far below the rounding of the stored float; this GPU's FP64
+// pipe made the FP64 functions the bulk of the kernel).
+template <typename R>
+__device__ __forceinline__ double init_log1p(double x) {
+  if constexpr (sizeof(R) == 4) return lbm::to_double(lbm::m_log1p(lbm::to_df(x)));
+  else return log1p(x);
+}
+template <typename R>
+__device__ __forceinline__ double init_expm1(double x) {
+  if constexpr (sizeof(R) == 4) return lbm::to_double(lbm::m_expm1(lbm::to_df(x)));
+  else return expm1(x);
+}
+
 // Equilibrium populations from (rho, u, p) (from_p = 1) or (rho, u, s) (from_p = 0), computed in
-// FP64 and stored shifted by the rest populations.
+// FP64 (the logarithms and the exponential as above) and stored shifted by the rest populations.
 template <typename R>
 __global__ void init_kernel(const double* __restrict__ rho_in, const double* __restrict__ u_in,
                             const double* __restrict__ x_in, int from_p, R* __restrict__ st,
@@ -186,10 +203,10 @@ __global__ void init_kernel(const double* __restrict__ rho_in, const double* __r
   if (i >= plane) return;
   const LatDev& d = lat[lattice_of_node(lat, B, i)];
   const double rho = rho_in[i], u = u_in[i];
-  const double lnr = log(rho / a.rho0);
-  const double ds = from_p ? (a.cp / a.gamma) * log(x_in[i] / a.p0) - a.cp * lnr : x_in[i] - d.s0;
+  const double lnr = init_log1p<R>((rho - a.rho0) * a.inv_rho0);
+  const double ds = from_p ? a.cp_over_gamma * init_log1p<R>((x_in[i] - a.p0) * a.inv_p0) - a.cp * lnr : x_in[i] - d.s0;
   const double s = d.s0 + ds;
-  const double pt = a.p0 * expm1(a.gamma * (lnr + ds / a.cp));
+  const double pt = a.p0 * init_expm1<R>(a.gamma * (lnr + ds * a.inv_cp));
   const double rt = rho - a.rho0, J = rho * u;
   const double zeta = rho * s, zt = zeta - d.zeta_r;
   const double l2 = a.lam * a.lam;
@@ -205,15 +222,19 @@ __global__ void init_kernel(const double* __restrict__ rho_in, const double* __r
     psi = zeta * u;
     eps_t = 2.0 * l2 * rho * (ds + a.cp_log * lnr) + e_t * s + a.e_r * ds;
   }
-  const double af = a.rho0, ag = a.rho0 * a.cp;
-  double r = rt / af, j = J / (af * a.lam), q = e_t / (af * l2);
-  st[0 * plane + i] = R((r - q) / 3.0);
-  st[1 * plane + i] = R((2.0 * r + q) / 6.0 + 0.5 * j);
-  st[2 * plane + i] = R((2.0 * r + q) / 6.0 - 0.5 * j);
-  r = zt / ag; j = psi / (ag * a.lam); q = eps_t / (ag * l2);
-  st[3 * plane + i] = R((r - q) / 3.0);
-  st[4 * plane + i] = R((2.0 * r + q) / 6.0 + 0.5 * j);
-  st[5 * plane + i] = R((2.0 * r + q) / 6.0 - 0.5 * j);
+  // Scaled moments, then M^-1 (eq. M-d1q3q3 inverted); the FP64 pipe of this GPU runs a division as a
+  // Newton sequence, so every scale is a product with a host-computed reciprocal.
+  const double third = 1.0 / 3.0, sixth = 1.0 / 6.0;
+  double r = rt * a.inv_af[0], j = J * a.inv_af[1], q = e_t * a.inv_af[2];
+  double h = (2.0 * r + q) * sixth;
+  st[0 * plane + i] = R((r - q) * third);
+  st[1 * plane + i] = R(h + 0.5 * j);
+  st[2 * plane + i] = R(h - 0.5 * j);
+  r = zt * a.inv_ag[0]; j = psi * a.inv_ag[1]; q = eps_t * a.inv_ag[2];
+  h = (2.0 * r + q) * sixth;
+  st[3 * plane + i] = R((r - q) * third);
+  st[4 * plane + i] = R(h + 0.5 * j);
+  st[5 * plane + i] = R(h - 0.5 * j);
 }
 
 // Moments (absolute) per node; any output may be null.
@@ -471,6 +492,17 @@ InitArgs init_args(const lbm_ctx* c) {
   a.a1 = c->ph.lin_a1();
   a.b1 = c->ph.lin_b1();
   a.c02 = c->ph.c02();
+  a.inv_rho0 = 1.0 / c->ph.rho0;
+  a.inv_p0 = 1.0 / c->ph.p0;
+  a.inv_cp = 1.0 / c->ph.cp;
+  a.cp_over_gamma = c->ph.cp / c->ph.gamma;
+  const double af = c->ph.rho0, ag = c->ph.rho0 * c->ph.cp, l = c->ph.lam;
+  a.inv_af[0] = 1.0 / af;
+  a.inv_af[1] = 1.0 / (af * l);
+  a.inv_af[2] = 1.0 / (af * l * l);
+  a.inv_ag[0] = 1.0 / ag;
+  a.inv_ag[1] = 1.0 / (ag * l);
+  a.inv_ag[2] = 1.0 / (ag * l * l);
   return a;
 }
 

@@ -121,6 +121,30 @@ def test_shocks_fp32_l1(O, lbm):
         assert np.mean(np.abs(np.asarray(g[0]) - ref[:, 0])) <= 1e-4
 
 
+def test_fp32_initial_state_is_the_rounded_fp64_equilibrium(O, lbm):
+    """FP32 storage: the initialisation takes its logarithms and exponential in double-float (about 48
+    bits; series, or the FP64 functions for |rho/rho0 - 1| > 0.3) and the rest in FP64, then rounds
+    once, so the stored shifted populations are the FP64 equilibrium of the oracle rounded to float,
+    but for a rare tie-break of one float ulp."""
+    ph = O.default_phys()
+    rng = np.random.default_rng(12)
+    N = 20000
+    rho = np.concatenate([1 + 0.1 * rng.standard_normal(N // 2), rng.uniform(0.3, 1.9, N - N // 2)])
+    u = 0.1 * rng.standard_normal(N)
+    p = ph.p0 * rho ** 1.4 * rng.uniform(0.7, 1.3, N)
+    lat = lbm.Lattice(N, s_e=1.2, precision="f32")
+    lat.set_state(rho, u, p)
+    got = lat.populations()  # stored float + rest population, in FP64
+    lat.close()
+    w = O.init(ph, np.full(4, ph.rho0), np.zeros(4), p=np.full(4, ph.p0))[0][:, None]  # rest state
+    shift = (O.init(ph, rho, u, p=p).T - w).astype(np.float32)
+    want = shift.astype(np.float64) + w
+    ulp = np.spacing(np.abs(shift)).astype(np.float64)
+    err = np.abs(got - want)
+    assert np.all(err <= ulp + 4e-16)
+    assert np.mean(err <= 4e-16) >= 0.999
+
+
 def test_fp32_paired_lane_layouts_agree(O, lbm):
     """FP32 with two nodes per thread (one float2 lane: nodes 0, 1) and four (two lanes: nodes 0, 2 and
     1, 3) pairs different nodes on a lane, so the two layouts only agree when every node gets the same
