@@ -74,10 +74,16 @@ __device__ __forceinline__ df fm(df x, df y, df z) {
   t = __fadd_rn(t, __fadd_rn(e, z.lo));
   return fast_two_sum(s, t);
 }
-// 1/x: the correctly rounded FP32 reciprocal y of x.hi, then one Newton step y (1 + r) with the
-// residual r = 1 - x y evaluated exactly to first order (FMA-based product error).
+// FP32 reciprocal of a to within about an ulp: the hardware approximation and one Newton step.
+__device__ __forceinline__ float rcp_f32(float a) {
+  const float y = rcp_approx(a);
+  return __fmaf_rn(y, __fmaf_rn(-a, y, 1.0f), y);
+}
+
+// 1/x: the FP32 reciprocal y of x.hi, then one Newton step y (1 + r) with the residual r = 1 - x y
+// evaluated exactly to first order (FMA-based product error).
 __device__ __forceinline__ df m_rcp(df x) {
-  const float y = __frcp_rn(x.hi);
+  const float y = rcp_f32(x.hi);
   const float p = __fmul_rn(x.hi, y);
   const float e = __fmaf_rn(x.hi, y, -p);
   const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), e), __fmul_rn(x.lo, y));
@@ -202,7 +208,8 @@ __device__ __forceinline__ df2 fm(df2 x, df2 y, df2 z) {
   return fast_two_sum(s, t);
 }
 __device__ __forceinline__ df2 m_rcp(df2 x) {
-  const float2 y = make_float2(__frcp_rn(x.hi.x), __frcp_rn(x.hi.y));
+  float2 y = make_float2(rcp_approx(x.hi.x), rcp_approx(x.hi.y));
+  y = p_fma(y, p_fma(p_neg(x.hi), y, make_float2(1.0f, 1.0f)), y);
   const float2 p = p_mul(x.hi, y);
   const float2 e = p_fma(x.hi, y, p_neg(p));
   const float2 r = p_sub(p_sub(p_sub(make_float2(1.0f, 1.0f), p), e), p_mul(x.lo, y));
