@@ -141,8 +141,8 @@ __device__ __forceinline__ df m_expm1(df x) {
 // ---------------------------------------------------------------------------------------------------
 // Two double-floats on paired FP32 lanes: df2 holds nodes (x, y) as hi = (hi_x, hi_y), lo = (lo_x, lo_y),
 // and every operation above runs on FFMA2 / FADD2 / FMUL2, lane by lane the same FP32 operations in the
-// same order (a negation is an exact multiplication by -1), so a df2 result equals the two df results
-// bit for bit.
+// same order (a negation is a sign flip of each half, as in the scalar code), so a df2 result equals
+// the two df results bit for bit.
 struct df2 {
   float2 hi, lo;
 };
@@ -151,7 +151,7 @@ __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p_neg(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 __device__ __forceinline__ df df2_get(const df2& v, int j) { return j ? df{v.hi.y, v.lo.y} : df{v.hi.x, v.lo.x}; }
 __device__ __forceinline__ void df2_set(df2& v, int j, df a) {
