@@ -50,10 +50,11 @@ FLOPS_PER_NODE = {"f32": 110.0, "f64": (2 * 507.31008e6 + 194.468864e6 + 194.468
 # Peak arithmetic per SM per clock from the unit counts: 128 FP32 FMA lanes (256 flops); FP64 at
 # 2 FMA per SM per clock (4 flops; the nominal 1.25 TFLOP/s of the part at 152 SMs, 2.07 GHz).
 FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
-# FP32 operations (FADD + FMUL + FFMA, each one lane-operation) per computed node-step of the
-# double-float step kernel, from ncu at N = 2^23, (8, 256, 1): (49,009,766,400 FADD + 13,958,963,200
-# FFMA + 4,831,948,800 FMUL) over 37,450 x 256 x 8 node-steps = 884.0 (profiles/step_tiles_df_N8M.md).
-DF_FP32_OPS_PER_COMPUTED = 67800678400 / 76697600
+# FP32 operations (each lane of FADD2 / FFMA2 / FMUL2 one lane-operation) per computed node-step of
+# the double-float step kernel on paired lanes, from ncu at N = 2^23, (8, 128, 4): 2 x (9,198,774,272
+# FADD2 + 19,972,435,968 FFMA2 + 2,326,538,240 FMUL2) thread-instructions over 17,477 x 512 x 8
+# node-steps = 880.0 (profiles/step_tiles_df_N8M.md).
+DF_FP32_OPS_PER_COMPUTED = 2 * (9198774272 + 19972435968 + 2326538240) / (17477 * 512 * 8)
 TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.51424e6 + 149.390848e6) / 8388608,
                           ("f64", 1, 256, 2): (403.07968e6 + 347.049472e6) / 8388608}
 
