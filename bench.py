@@ -15,6 +15,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -78,7 +79,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # The raw samples go to LBM_CLOCKS_DIR (default: the system's temporary directory).
+        out_dir = os.environ.get("LBM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{device_index}.csv")
 
     def __enter__(self):
         try:
