@@ -20,7 +20,7 @@ namespace lbm {
 
 // Lanes: a thread holds W consecutive nodes in one lane value X (W = 1: X = double, float, or df,
 // the double-float of lbm_df.cuh over FP64 storage; W = 2: X = float2, two nodes on Blackwell's paired
-// FP32 instructions). R is the storage type.
+// FP32 instructions, or df2, two double-float nodes on them). R is the storage type.
 template <typename X>
 struct Lane {
   using R = X;
@@ -36,10 +36,16 @@ struct Lane<df> {
   using R = double;
   static constexpr int W = 1;
 };
+template <>
+struct Lane<df2> {
+  using R = double;
+  static constexpr int W = 2;
+};
 __device__ __forceinline__ double lget(double x, int) { return x; }
 __device__ __forceinline__ float lget(float x, int) { return x; }
 __device__ __forceinline__ float lget(float2 x, int j) { return j ? x.y : x.x; }
 __device__ __forceinline__ double lget(df x, int) { return to_double(x); }
+__device__ __forceinline__ double lget(df2 x, int j) { return to_double(df2_get(x, j)); }
 __device__ __forceinline__ void lset(double& x, int, double v) { x = v; }
 __device__ __forceinline__ void lset(float& x, int, float v) { x = v; }
 __device__ __forceinline__ void lset(float2& x, int j, float v) {
@@ -47,23 +53,43 @@ __device__ __forceinline__ void lset(float2& x, int j, float v) {
   else x.x = v;
 }
 __device__ __forceinline__ void lset(df& x, int, double v) { x = to_df(v); }
+__device__ __forceinline__ void lset(df2& x, int j, double v) { df2_set(x, j, to_df(v)); }
 template <typename X>
 __device__ __forceinline__ X lit(double v) {
-  if constexpr (Lane<X>::W == 2) return make_float2((float)v, (float)v);
-  else if constexpr (std::is_same<X, df>::value) return df_from_double_host(v);  // folded for constants
-  else return X(v);
+  if constexpr (std::is_same<X, df2>::value) {
+    const df a = df_from_double_host(v);  // folded for constants
+    return df2_of(a, a);
+  } else if constexpr (Lane<X>::W == 2) {
+    return make_float2((float)v, (float)v);
+  } else if constexpr (std::is_same<X, df>::value) {
+    return df_from_double_host(v);
+  } else {
+    return X(v);
+  }
 }
 template <typename X>
 __device__ __forceinline__ X lit_r(typename Lane<X>::R v) {
-  if constexpr (Lane<X>::W == 2) return make_float2(v, v);
-  else if constexpr (std::is_same<X, df>::value) return to_df(v);
-  else return v;
+  if constexpr (std::is_same<X, df2>::value) {
+    const df a = to_df(v);
+    return df2_of(a, a);
+  } else if constexpr (Lane<X>::W == 2) {
+    return make_float2(v, v);
+  } else if constexpr (std::is_same<X, df>::value) {
+    return to_df(v);
+  } else {
+    return v;
+  }
 }
 // Per-lane select: lane j takes a where b[j], else keeps x.
 template <typename X>
 __device__ __forceinline__ X sel(const bool (&b)[Lane<X>::W], X a, X x) {
   if constexpr (Lane<X>::W == 1) {
     return b[0] ? a : x;
+  } else if constexpr (std::is_same<X, df2>::value) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      if (b[j]) df2_set(x, j, df2_get(a, j));
+    return x;
   } else {
 #pragma unroll
     for (int j = 0; j < Lane<X>::W; ++j)
@@ -96,6 +122,9 @@ template <typename X, int NT>
 __device__ __forceinline__ X left_of(const X* arr, int t, X own) {
   if constexpr (Lane<X>::W == 1) {
     return t > 0 ? arr[t - 1] : own;
+  } else if constexpr (std::is_same<X, df2>::value) {
+    const df x0 = df2_get(own, 0);
+    return df2_of(t > 0 ? df2_get(arr[t - 1], 1) : x0, x0);
   } else {
     return make_float2(t > 0 ? arr[t - 1].y : own.x, own.x);
   }
@@ -104,6 +133,9 @@ template <typename X, int NT>
 __device__ __forceinline__ X right_of(const X* arr, int t, X own) {
   if constexpr (Lane<X>::W == 1) {
     return t < NT - 1 ? arr[t + 1] : own;
+  } else if constexpr (std::is_same<X, df2>::value) {
+    const df x1 = df2_get(own, 1);
+    return df2_of(x1, t < NT - 1 ? df2_get(arr[t + 1], 0) : x1);
   } else {
     return make_float2(own.y, t < NT - 1 ? arr[t + 1].x : own.y);
   }
@@ -283,7 +315,7 @@ __device__ __forceinline__ void adjoint_node_step(const X (&f)[6], const X (&a)[
 // Paired FP32 lanes: at least six CTAs of 128 threads per SM (at most 85 registers; the compiler takes
 // 80 with a 20-byte spill), measured 1.6 % faster than the five CTAs its own register choice allows.
 template <typename X, int NT>
-__global__ void __launch_bounds__(NT, Lane<X>::W == 2 ? 6 : 0) adjoint_block_kernel(const typename Lane<X>::R* __restrict__ f0,
+__global__ void __launch_bounds__(NT, std::is_same<X, float2>::value ? 6 : 0) adjoint_block_kernel(const typename Lane<X>::R* __restrict__ f0,
                                                            const typename Lane<X>::R* __restrict__ a_next,
                                                            typename Lane<X>::R* __restrict__ a_out, long long plane,
                                                            const LatDev* __restrict__ lat, int B, long long ntiles,
@@ -578,7 +610,9 @@ cudaError_t launch_adjoint_block_df(const double* f0, const double* a_next, doub
                                     double* grad_tile, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   if (K < 1 || K > kAdjointMaxK) return cudaErrorInvalidValue;
-  return launch_block_lanes<df>(f0, a_next, a_out, plane, lat, B, ntiles, K, c, grad_tile, st);
+  // Two nodes per thread on paired FP32 lanes (df2): lane for lane the operations of one node per
+  // thread, on the same 256-node tiles.
+  return launch_block_lanes<df2>(f0, a_next, a_out, plane, lat, B, ntiles, K, pair_consts(c), grad_tile, st);
 }
 
 template <typename R>

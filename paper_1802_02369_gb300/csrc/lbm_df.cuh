@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -279,6 +281,19 @@ template <>
 __device__ __forceinline__ df2 num<df2>(double v) {
   const df a = num<df>(v);
   return df2{make_float2(a.hi, a.hi), make_float2(a.lo, a.lo)};
+}
+
+// Consts<df2> from Consts<df>: every double-float field on both lanes (host).
+inline Consts<df2> pair_consts(const Consts<df>& c) {
+  constexpr size_t n = offsetof(Consts<df>, eq_mode) / sizeof(df);
+  static_assert(offsetof(Consts<df2>, eq_mode) == n * sizeof(df2), "Consts layout");
+  Consts<df2> p;
+  const df* s = reinterpret_cast<const df*>(&c);
+  df2* t = reinterpret_cast<df2*>(&p);
+  for (size_t i = 0; i < n; ++i) t[i] = df2{make_float2(s[i].hi, s[i].hi), make_float2(s[i].lo, s[i].lo)};
+  p.eq_mode = c.eq_mode;
+  p.source_on = c.source_on;
+  return p;
 }
 
 // Step kernel in double-float (lbm_step_df.cu): FP64 storage, tiles of NT*V nodes, K steps per launch.

@@ -8,8 +8,6 @@
 // loaded, the dimensionless node update of lbm_internal.cuh runs on df lanes, and the populations are
 // summed back to FP64 when the tile is stored. Neighbour values cross threads by two shuffles (hi, lo)
 // and warps through shared memory.
-#include <cstddef>
-
 #include "lbm_df.cuh"
 #include "lbm_internal.cuh"
 
@@ -208,19 +206,6 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
       for (int i = 0; i < 6; ++i) dst[i * plane] = to_double(df2_get(f[v >> 1][i], v & 1));
     }
   }
-}
-
-// Consts<df2> from Consts<df>: every double-float field on both lanes.
-Consts<df2> pair_consts(const Consts<df>& c) {
-  constexpr size_t n = offsetof(Consts<df>, eq_mode) / sizeof(df);
-  static_assert(offsetof(Consts<df2>, eq_mode) == n * sizeof(df2), "Consts layout");
-  Consts<df2> p;
-  const df* s = reinterpret_cast<const df*>(&c);
-  df2* t = reinterpret_cast<df2*>(&p);
-  for (size_t i = 0; i < n; ++i) t[i] = df2{make_float2(s[i].hi, s[i].hi), make_float2(s[i].lo, s[i].lo)};
-  p.eq_mode = c.eq_mode;
-  p.source_on = c.source_on;
-  return p;
 }
 
 template <int NT, int V>
