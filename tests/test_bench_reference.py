@@ -3,6 +3,7 @@ prints the contract's JSON line; under a two-rank launch rank 0 alone runs it an
 Both run on the CPU."""
 import json
 import os
+import socket
 import subprocess
 import sys
 
@@ -32,8 +33,14 @@ def test_reference_arm_prints_the_contract_line():
     _check_line(lines[0], 1)
 
 
+def _free_port() -> int:
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
 def test_reference_arm_two_ranks_prints_once():
-    port = 29600 + (os.getpid() % 300)
+    port = _free_port()
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
                         "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
                         "--gpus", "2", "--steps", "1", "--warmup", "3"],
