@@ -96,18 +96,50 @@ class RaggedBatch:
         return self.rho[lo:hi], self.u[lo:hi], self.p[lo:hi]
 
 
+def entropy_of_state(rho, p_rel, gamma: float = 1.4, cp: float = 1.0, rho0: float = 1.0):
+    """Specific entropy s - s0 of an ideal-gas state of density rho and pressure p_rel * p_unit,
+    measured from the isentrope through (rho0, p_unit): (c_p / gamma) log(p_rel (rho0 / rho)^gamma).
+    Used only to select Riemann data (a property of the drawn inputs)."""
+    return (cp / gamma) * (np.log(p_rel) - gamma * np.log(np.asarray(rho) / rho0))
+
+
 def ragged_batch(B: int, seed: int, p_unit: float, n_min: int = 512, n_max: int = 65536,
-                 s_range=(1.0, 1.9), left=(0.8, 1.2), right=(0.3, 0.7), p_bounce: float = 0.5) -> RaggedBatch:
+                 s_range=(1.0, 1.9), left=(0.8, 1.2), right=(0.3, 0.7), p_bounce: float = 0.5,
+                 entropy_range=None, gamma: float = 1.4) -> RaggedBatch:
     """B Riemann problems of uneven lengths: N_b uniform in [n_min, n_max], s_e uniform in
     s_range, left state (rho, p) uniform in ``left``, right state uniform in ``right`` (pressures
     times p_unit), u = 0, split at N_b / 2; boundary periodic or bounce-back with probability
-    p_bounce each."""
+    p_bounce each.
+
+    entropy_range = (lo, hi): keep only the draws whose left and right states both have a specific
+    entropy (``entropy_of_state``, c_p = 1) in [lo, hi]. Candidates are drawn from the same
+    distribution in chunks from the same generator and the first B accepted ones are kept, so the
+    result is the conditional distribution of the unfiltered draw."""
     rng = np.random.default_rng(np.random.PCG64(seed))
-    lengths = rng.integers(n_min, n_max + 1, B).astype(np.int64)
-    s_e = rng.uniform(s_range[0], s_range[1], B)
-    states = np.stack([rng.uniform(*left, B), rng.uniform(*left, B),
-                       rng.uniform(*right, B), rng.uniform(*right, B)], axis=1)
-    bc = (rng.uniform(0, 1, B) < p_bounce).astype(np.int32)
+    if entropy_range is None:
+        lengths = rng.integers(n_min, n_max + 1, B).astype(np.int64)
+        s_e = rng.uniform(s_range[0], s_range[1], B)
+        states = np.stack([rng.uniform(*left, B), rng.uniform(*left, B),
+                           rng.uniform(*right, B), rng.uniform(*right, B)], axis=1)
+        bc = (rng.uniform(0, 1, B) < p_bounce).astype(np.int32)
+    else:
+        lo, hi = entropy_range
+        keep = [[], [], [], []]
+        got = 0
+        while got < B:
+            C = 8192
+            ln = rng.integers(n_min, n_max + 1, C).astype(np.int64)
+            se = rng.uniform(s_range[0], s_range[1], C)
+            st = np.stack([rng.uniform(*left, C), rng.uniform(*left, C),
+                           rng.uniform(*right, C), rng.uniform(*right, C)], axis=1)
+            bb = (rng.uniform(0, 1, C) < p_bounce).astype(np.int32)
+            sl = entropy_of_state(st[:, 0], st[:, 1], gamma)
+            sr = entropy_of_state(st[:, 2], st[:, 3], gamma)
+            ok = (sl >= lo) & (sl <= hi) & (sr >= lo) & (sr <= hi)
+            for lst, arr in zip(keep, (ln, se, st, bb)):
+                lst.append(arr[ok])
+            got += int(ok.sum())
+        lengths, s_e, states, bc = (np.concatenate(lst)[:B] for lst in keep)
     offsets = np.zeros(B + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(lengths)
     tot = int(offsets[-1])

@@ -36,6 +36,18 @@ MUTANTS = {
     "linear eps_eq rho constant": ("+ 3.0 * s0 * c02 + 2.0 - 2.0 * s0 - 2.0 / g) * rho",
                                    "+ 3.0 * s0 * c02 + 2.0 - 2.0 * s0) * rho"),
     "linear eps_eq zeta coefficient": ("3.0 * (cp * u0 * u0 + s0 * c02) * zeta;", "3.0 * (cp * u0 * u0) * zeta;"),
+    "kappa drops Pr": ("const R kappa = rho * nu * ph.cp / ph.Pr;", "const R kappa = rho * nu * ph.cp;"),
+    "coupled rate drops Pr": ("const double sigma_psi = 1.5 * (gamma / Pr) * sigma_e;",
+                              "const double sigma_psi = 1.5 * gamma * sigma_e;"),
+    "T0 drops rho0": ("return ph.p0 / (ph.rho0 * gas_r(ph));", "return ph.p0 / gas_r(ph);"),
+    "EOS drops rho0": ("p = ph.p0 * pow(rho / ph.rho0, ph.gamma)", "p = ph.p0 * pow(rho, ph.gamma)"),
+    "gas constant": ("return ph.cp * (1.0 - 1.0 / ph.gamma);", "return ph.cp / ph.gamma;"),
+    "entropy from pressure drops 1/gamma": ("s[j] = ph->s0 + (ph->cp / ph->gamma) * std::log(",
+                                            "s[j] = ph->s0 + ph->cp * std::log("),
+    "total energy kinetic doubled": ("a[3] += p / (ph->gamma - 1.0) + 0.5 * rho * u * u;",
+                                     "a[3] += p / (ph->gamma - 1.0) + rho * u * u;"),
+    "total energy internal coefficient": ("a[3] += p / (ph->gamma - 1.0) + 0.5 * rho * u * u;",
+                                          "a[3] += p / ph->gamma + 0.5 * rho * u * u;"),
 }
 
 
@@ -52,7 +64,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_linear.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_linear.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_stability.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
 

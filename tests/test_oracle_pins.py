@@ -113,8 +113,9 @@ def test_phase_speeds_are_euler_characteristics(O, rho, u0, s):
     np.testing.assert_allclose(speeds, np.sort([u0 - c, u0, u0 + c]), rtol=0, atol=1e-5)
 
 
-@pytest.mark.parametrize("s_e,lam", [(1.2, 1.0), (1.5, 1.0), (1.9, 1.0), (1.5, 2.0)])
-def test_second_order_damping(O, s_e, lam):
+@pytest.mark.parametrize("s_e,lam,gamma,Pr", [(1.2, 1.0, 1.4, 1.0), (1.5, 1.0, 1.4, 1.0), (1.9, 1.0, 1.4, 1.0),
+                                             (1.5, 2.0, 1.4, 1.0), (1.5, 1.0, 1.3, 0.71), (1.2, 2.0, 1.67, 2.0)])
+def test_second_order_damping(O, s_e, lam, gamma, Pr):
     """Damping of the conserved modes at rest (u0 = 0, s = 0) against the second-order equivalent
     equations eq. (edp-ordre-2) with the defects eq. (thetas) and the tensor eq. (Lambda-d1q3q3).
 
@@ -124,8 +125,9 @@ def test_second_order_damping(O, s_e, lam):
         D_zz = sigma_psi dt (2 lambda^2/3 + c0^2/gamma),
     so an acoustic mode decays at (D_JJ + D_zr / c_p)/2 and the entropy mode at D_zz - D_zr / c_p
     (first-order perturbation of the Euler eigenvalues), with sigma = 1/s - 1/2 (eq. henon) and
-    sigma_psi = (3/2)(gamma/Pr) sigma_e (eq. lien-sigma-sigma)."""
-    ph = O.default_phys(lam=lam)
+    sigma_psi = (3/2)(gamma/Pr) sigma_e (eq. lien-sigma-sigma). Away from gamma/Pr = 1.4 the coupled
+    rate s_psi changes D_zr and D_zz, which pins the Pr and gamma factors of the coupling."""
+    ph = O.default_phys(lam=lam, gamma=gamma, Pr=Pr)
     r = O.coupled_rates(s_e, ph.gamma, ph.Pr)
     g, c0, dt, cp = ph.gamma, lam / 2, 1.0 / lam, ph.cp
     sig_e = 1 / s_e - 0.5
@@ -221,6 +223,64 @@ def test_cp_covariance(O):
     np.testing.assert_allclose(mb[:, 2:3], 2.5 * ma[:, 2:3], atol=5e-14)
 
 
+def test_initial_pressure_round_trip(O):
+    """Initialising from (rho, u = 0, p) inverts eq. (gaz-parfait) for the specific entropy; at rest the
+    energy equilibrium of eq. (energie-equilibre) is 3 p - 2 lambda^2 rho, so it must return the given
+    pressure (non-adiabatic data, so that the inversion is exercised away from s = s0)."""
+    rng = np.random.default_rng(41)
+    for lam, gamma, cp, rho0, s0 in ((1.0, 1.4, 1.0, 1.0, 0.0), (2.0, 1.3, 2.5, 1.3, -0.1)):
+        ph = O.default_phys(lam=lam, gamma=gamma, cp=cp, rho0=rho0, s0=s0)
+        N = 32
+        rho = rho0 * rng.uniform(0.5, 1.5, N)
+        p = ph.p0 * rng.uniform(0.4, 1.6, N)
+        e_eq = O.equilibria(ph, O.init(ph, rho, np.zeros(N), p=p))[:, 0]
+        np.testing.assert_allclose((e_eq + 2 * lam ** 2 * rho) / 3, p, rtol=1e-13)
+
+
+def test_rho0_covariance(O):
+    """Scaling the reference density and pressure (rho0, p0) -> (k rho0, k p0) together with the
+    data rho -> k rho at fixed u and s scales p by k (eq. gaz-parfait) and leaves T = p/(rho r) and
+    T0 = p0/(rho0 r) unchanged; every moment (rho, J, zeta = rho s, e_eq, psi_eq, eps_eq and the source,
+    whose kappa = rho nu c_p / Pr is proportional to rho) then scales by k, as does M of
+    eq. (M-d1q3q3), so the populations are identical at every step."""
+    r = O.coupled_rates(1.4)
+    ph1 = O.default_phys()
+    _, rho, u, s = _smooth_state(O, ph1, 40, seed=19, amp=0.05)
+    a = O.run(ph1, r, O.init(ph1, rho, u, s=s), 200)
+    for k in (1.7, 0.6):
+        phk = O.default_phys(rho0=k, p0=k * ph1.p0)
+        b = O.run(phk, r, O.init(phk, k * rho, u, s=s), 200)
+        np.testing.assert_allclose(b, a, rtol=0, atol=5e-14)
+
+
+def test_total_energy_kinetic_part_is_galilean(O):
+    """The total energy of the diagnostics, sum of rho E over the lattice, of a uniform state moving at
+    u exceeds that of the same state at rest (same rho and s) by exactly the kinetic energy of a rigid
+    translation, N rho u^2 / 2."""
+    ph = O.default_phys()
+    N = 16
+    for rho, s, u in ((1.0, 0.0, 0.1), (0.7, -0.2, -0.25), (1.3, 0.1, 0.05)):
+        e_rest = O.diagnostics(ph, L.uniform_state(ph, rho, 0.0, s, N))[0][3]
+        e_move = O.diagnostics(ph, L.uniform_state(ph, rho, u, s, N))[0][3]
+        assert abs((e_move - e_rest) - N * rho * u * u / 2) <= 1e-13 * N
+
+
+def test_total_energy_internal_part_obeys_gibbs(O):
+    """At rest the total energy is the internal energy, whose derivative in the specific entropy at
+    fixed density is rho T (Gibbs relation de = T ds + p / rho^2 drho), with T from the gas law
+    p = rho r T, r = c_p (1 - 1/gamma), and p from eq. (gaz-parfait)."""
+    N, h = 8, 1e-5
+    for gamma, cp, rho0 in ((1.4, 1.0, 1.0), (1.3, 2.5, 1.3)):
+        ph = O.default_phys(gamma=gamma, cp=cp, rho0=rho0)
+        for rho, s in ((1.0, 0.0), (0.6, -0.3), (1.4, 0.2)):
+            rho = rho * rho0
+            ep = O.diagnostics(ph, L.uniform_state(ph, rho, 0.0, s + h, N))[0][3]
+            em = O.diagnostics(ph, L.uniform_state(ph, rho, 0.0, s - h, N))[0][3]
+            p = ph.p0 * (rho / ph.rho0) ** gamma * np.exp(gamma * (s - ph.s0) / cp)
+            T = p / (rho * cp * (1 - 1 / gamma))
+            assert abs((ep - em) / (2 * h) / (N * rho * T) - 1) < 1e-8
+
+
 def test_step_independent_of_dx(O):
     """With nu = sigma_e lambda dx (eq. nu-d1q3q3), dt = dx / lambda and centred differences, the
     step in lattice units does not depend on dx."""
@@ -231,26 +291,31 @@ def test_step_independent_of_dx(O):
     np.testing.assert_allclose(O.run(ph2, r, fd, 120), O.run(ph1, r, fd, 120), rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("lam,dx", [(1.0, 1.0), (2.0, 0.5), (0.5, 1.0 / 40)])
-def test_entropy_production_closed_form(O, lam, dx):
+@pytest.mark.parametrize("lam,dx,gamma,Pr,rho0", [(1.0, 1.0, 1.4, 1.0, 1.0), (2.0, 0.5, 1.4, 1.0, 1.0),
+                                                  (0.5, 1.0 / 40, 1.4, 1.0, 1.0), (1.0, 1.0, 1.3, 0.71, 1.0),
+                                                  (2.0, 0.5, 1.67, 0.71, 1.3)])
+def test_entropy_production_closed_form(O, lam, dx, gamma, Pr, rho0):
     """One step of a small progressive wave u = c0 d sin(k x), rho = rho0 (1 + d sin(k x)),
     adiabatic: the collision keeps zeta and streaming permutes it, so the change of sum zeta is
     dt sum_j S_j with S of eq. (NS-rho-J-zeta). With T = T0 (rho/rho0)^(gamma-1), centred
     differences sin(k dx)/(k dx) times the exact gradients, and sum cos^2 = N/2 over a period:
         sum zeta(1) - sum zeta(0)
-            = dt nu d^2 k^2 (N/2) (sin(k dx)/(k dx))^2 (c0^2 / T0 + c_p (gamma-1)^2 / Pr)
-    up to O(d) relative corrections, with nu = sigma_e lambda dx (eq. nu-d1q3q3), dt = dx/lambda."""
+            = dt rho0 nu d^2 k^2 (N/2) (sin(k dx)/(k dx))^2 (c0^2 / T0 + c_p (gamma-1)^2 / Pr)
+    up to O(d) relative corrections, with nu = sigma_e lambda dx (eq. nu-d1q3q3), dt = dx/lambda,
+    kappa = rho nu c_p / Pr (the thermal term carries 1/Pr, the viscous one does not).
+    T0 = c0^2 / (c_p (gamma - 1)) follows from p0 = rho0 c0^2 / gamma and the gas law p = rho r T with
+    r = c_p (1 - 1/gamma), so the two terms stand in the ratio (gamma - 1) / Pr."""
     for s_e, N in ((1.9, 256), (1.2, 512), (1.5, 128)):
-        ph = O.default_phys(lam=lam, dx=dx)
+        ph = O.default_phys(lam=lam, dx=dx, gamma=gamma, Pr=Pr, rho0=rho0)
         g, c0, d = ph.gamma, ph.lam / 2, 1e-3
-        T0 = ph.p0 / (ph.rho0 * ph.cp * (1 - 1 / g))
-        rho, u, p = W.progressive_wave(N, d, c0, ph.p0)
+        T0 = c0 ** 2 / (ph.cp * (g - 1))
+        rho, u, p = W.progressive_wave(N, d, c0, ph.p0, gamma=g, rho0=rho0)
         fd = O.init(ph, rho, u, p=p)
         dz = O.diagnostics(ph, O.run(ph, O.coupled_rates(s_e), fd, 1))[0][2] - O.diagnostics(ph, fd)[0][2]
         k = 2 * np.pi / (N * dx)
         nu = (1 / s_e - 0.5) * lam * dx
         corr = (np.sin(k * dx) / (k * dx)) ** 2
-        pred = (dx / lam) * nu * d * d * k * k * (N / 2) * corr * (c0 ** 2 / T0 + ph.cp * (g - 1) ** 2 / ph.Pr)
+        pred = (dx / lam) * rho0 * nu * d * d * k * k * (N / 2) * corr * (c0 ** 2 / T0 + ph.cp * (g - 1) ** 2 / ph.Pr)
         assert abs(dz / pred - 1) < 2e-5
 
 
@@ -274,10 +339,10 @@ def test_entropy_energy_equilibrium_two_forms(O):
     """eq. (eq-energie-entropie-d1q3q3) in its log(T/T0) form equals the printed polytropic form
     eps_eq = 2 lambda^2 [rho (s - s0) + (1 - 1/gamma) c_p rho log(rho/rho0)] + [3(rho u^2 + p) - 2 lambda^2 rho] s."""
     rng = np.random.default_rng(21)
-    for lam, cp, s0 in ((1.0, 1.0, 0.0), (2.0, 1.7, 0.3)):
-        ph = O.default_phys(lam=lam, cp=cp, s0=s0)
+    for lam, cp, s0, rho0 in ((1.0, 1.0, 0.0, 1.0), (2.0, 1.7, 0.3, 1.0), (1.5, 1.2, -0.1, 1.3)):
+        ph = O.default_phys(lam=lam, cp=cp, s0=s0, rho0=rho0)
         N = 64
-        rho = rng.uniform(0.5, 1.5, N)
+        rho = rho0 * rng.uniform(0.5, 1.5, N)
         u = rng.uniform(-0.3, 0.3, N)
         s = rng.uniform(-0.5, 0.5, N)
         eq = O.equilibria(ph, O.init(ph, rho, u, s=s))
