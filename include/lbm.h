@@ -241,16 +241,27 @@ int lbm_adjoint_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch);
  * and the same flag bits, from populations the caller holds.
  *  fd: DEVICE pointer to float64 populations, plane-major [6][N] in the order (f0, f+, f-, g0, g+, g-)
  *      (the layout lbm_get_populations writes). N >= 1 and N <= 2^26 (else LBM_ERR_TOO_LARGE).
- *  lambda, phys: as for lbm_create (phys NULL = section 9 defaults; phys->s0 is the entropy reference).
+ *  lambda, phys: as for lbm_create (phys NULL = the lbm_phys defaults, see lbm_phys; phys->s0 is the
+ *      entropy reference).
  *  sums[4], flags[1]: both host or both device pointers. Host outputs: the call synchronises `stream`
  *      and returns LBM_ERR_UNSTABLE if a flag is set. Device outputs: the call only enqueues work.
  *  stream: cudaStream_t or NULL.
+ * fd, and sums/flags when they are device pointers, must be memory of the current device (or managed
+ * memory): memory of another GPU returns LBM_ERR_INVALID_ARG, as does a host fd. A CUDA error already
+ * pending on the calling thread (from the caller's earlier work) returns LBM_ERR_CUDA and is left in
+ * place; only this call's own failures are cleared.
  * The reduction scratch is a file-scope __device__ array of about 300 KB that every GPU loading the
  * library holds until exit; its address is looked up once per device on the first call with that
  * device current, so make the first call on each device before any stream capture. Every call
  * shares the array: calls whose kernels overlap on the GPU race (issue them on one stream). */
 int lbm_diagnostics_noalloc(const double *fd, int64_t N, double lambda, const lbm_phys *phys, double *sums,
                             int32_t *flags, void *stream);
+/* Test hook of the pointer-placement rule of lbm_diagnostics_noalloc, evaluated without any CUDA call:
+ * each pointer is described by its kind (0 host, 1 device memory, 2 managed memory) and, for device
+ * memory, its device ordinal; returns LBM_OK when the call would accept that placement on
+ * current_device, else LBM_ERR_INVALID_ARG. */
+int lbm_debug_noalloc_placement(int32_t current_device, int32_t fd_kind, int32_t fd_device, int32_t sums_kind,
+                                int32_t sums_device, int32_t flags_kind, int32_t flags_device);
 
 /* ------------------------------------------------------------------------------------------------
  * Finite-difference comparison solver (section 9). The paper checks its lattice Boltzmann results

@@ -126,13 +126,28 @@ __global__ void __launch_bounds__(kThreads) final_kernel(long long nchunks, Scra
   }
 }
 
-bool on_device(const void* p) {
+// Where a pointer lives: 0 host (or unknown to CUDA), 1 device memory of GPU `dev`, 2 managed memory.
+int pointer_kind(const void* p, int* dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+    cudaGetLastError();  // this call's own error (no earlier error is pending: checked on entry)
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  *dev = a.device;
+  if (a.type == cudaMemoryTypeDevice) return 1;
+  return a.type == cudaMemoryTypeManaged ? 2 : 0;
+}
+
+// The placement rule for the pointer arguments, from their kinds (pointer_kind) and devices: fd must
+// be device memory of the current device or managed memory; sums and flags must both be host, or
+// both device memory of the current device / managed memory. Returns LBM_OK or LBM_ERR_INVALID_ARG and
+// tells whether the outputs are on the device.
+int check_placement(int cur, int k_fd, int d_fd, int k_sums, int d_sums, int k_flags, int d_flags, bool* dev_out) {
+  if (k_fd == 0 || (k_fd == 1 && d_fd != cur)) return LBM_ERR_INVALID_ARG;
+  if ((k_sums != 0) != (k_flags != 0)) return LBM_ERR_INVALID_ARG;
+  if ((k_sums == 1 && d_sums != cur) || (k_flags == 1 && d_flags != cur)) return LBM_ERR_INVALID_ARG;
+  *dev_out = k_sums != 0;
+  return LBM_OK;
 }
 
 // Device address of the scratch array on the current device, looked up once per device.
@@ -158,9 +173,23 @@ extern "C" int lbm_diagnostics_noalloc(const double* fd, int64_t N, double lambd
                                        double* sums, int32_t* flags, void* stream) {
   if (!fd || !sums || !flags || N < 1 || !(lambda > 0.0)) return LBM_ERR_INVALID_ARG;
   if (N > kMaxChunks * kChunkNodes) return LBM_ERR_TOO_LARGE;
-  if (!on_device(fd)) return LBM_ERR_INVALID_ARG;
-  const bool dev_sums = on_device(sums), dev_flags = on_device(flags);
-  if (dev_sums != dev_flags) return LBM_ERR_INVALID_ARG;
+  // An error already pending on this thread belongs to earlier work of the caller: leave it in place
+  // (it would be indistinguishable from a failed launch of this call) and refuse to run.
+  if (cudaPeekAtLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  // Device memory must be on the current device (the scratch and the launches are); memory of
+  // another GPU would be a peer access. Managed memory is reachable from any device.
+  int d_fd = -1, d_sums = -1, d_flags = -1;
+  const int k_fd = pointer_kind(fd, &d_fd);
+  const int k_sums = pointer_kind(sums, &d_sums), k_flags = pointer_kind(flags, &d_flags);
+  bool dev_out = false;
+  if (check_placement(cur, k_fd, d_fd, k_sums, d_sums, k_flags, d_flags, &dev_out) != LBM_OK)
+    return LBM_ERR_INVALID_ARG;
+  const bool dev_sums = dev_out, dev_flags = dev_out;
   Scratch* s = nullptr;
   int rc = scratch_for_current_device(&s);
   if (rc != LBM_OK) return rc;
@@ -175,6 +204,7 @@ extern "C" int lbm_diagnostics_noalloc(const double* fd, int64_t N, double lambd
   cudaStream_t st = (cudaStream_t)stream;
   const long long nchunks = (N + kChunkNodes - 1) / kChunkNodes;
   chunk_kernel<<<(unsigned)nchunks, kThreads, 0, st>>>(fd, N, c, s);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;  // this launch's error only (none was pending)
   final_kernel<<<1, kThreads, 0, st>>>(nchunks, s, dev_sums ? sums : nullptr, dev_flags ? (int*)flags : nullptr);
   if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
   if (!dev_sums) {
@@ -187,4 +217,13 @@ extern "C" int lbm_diagnostics_noalloc(const double* fd, int64_t N, double lambd
     if (*flags) return LBM_ERR_UNSTABLE;
   }
   return LBM_OK;
+}
+
+// Test hook: the placement rule alone, without any CUDA call (kinds: 0 host, 1 device, 2 managed).
+extern "C" int lbm_debug_noalloc_placement(int32_t current_device, int32_t fd_kind, int32_t fd_device,
+                                           int32_t sums_kind, int32_t sums_device, int32_t flags_kind,
+                                           int32_t flags_device) {
+  bool dev_out = false;
+  return check_placement(current_device, fd_kind, fd_device, sums_kind, sums_device, flags_kind, flags_device,
+                         &dev_out);
 }

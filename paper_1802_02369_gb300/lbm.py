@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
             "lbm_save": (i32, [vp, ctypes.c_char_p]),
             "lbm_load": (i32, [vp, ctypes.c_char_p]),
             "lbm_diagnostics_noalloc": (i32, [vp, i64, d, P(lbm_phys), vp, vp, vp]),
+            "lbm_debug_noalloc_placement": (i32, [i32] * 7),
             "lbm_set_mode": (i32, [vp, i32]),
             "lbm_debug_eval_f32": (i32, [vp, vp, i64, i32, vp]),
             "lbm_debug_eval_df": (i32, [vp, vp, vp, i64, i32, vp]),

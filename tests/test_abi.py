@@ -59,3 +59,28 @@ def test_invalid_arguments_are_rejected_without_gpu(lib_path):
     assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(bad), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_total_nodes(None) == -1
+
+
+def test_noalloc_pointer_placement_rule(lib_path):
+    """lbm_diagnostics_noalloc accepts populations in device memory of the current device (or managed
+    memory) and outputs both on the host or both on the current device; memory of another GPU, a host
+    fd and mixed outputs are refused. The rule is evaluated by its test hook, with no CUDA call."""
+    from paper_1802_02369_gb300 import lbm
+
+    lib = lbm.load_library(lib_path)
+    ok, bad = lbm.LBM_OK, lbm.LBM_ERR_INVALID_ARG
+    H, D, M = 0, 1, 2
+    cases = [
+        ((0, D, 0, H, -1, H, -1), ok),      # device fd, host outputs
+        ((0, D, 0, D, 0, D, 0), ok),        # everything on the current device
+        ((1, D, 1, D, 1, M, 0), ok),        # device 1 current; managed flags
+        ((0, M, 1, H, -1, H, -1), ok),      # managed fd allocated on another device
+        ((0, H, -1, H, -1, H, -1), bad),    # host fd
+        ((0, D, 1, H, -1, H, -1), bad),     # fd on another GPU
+        ((1, D, 1, D, 0, D, 1), bad),       # sums on another GPU
+        ((1, D, 1, D, 1, D, 0), bad),       # flags on another GPU
+        ((0, D, 0, D, 0, H, -1), bad),      # mixed outputs
+        ((0, D, 0, H, -1, M, 0), bad),
+    ]
+    for args, want in cases:
+        assert lib.lbm_debug_noalloc_placement(*args) == want, args
