@@ -103,27 +103,74 @@ def entropy_of_state(rho, p_rel, gamma: float = 1.4, cp: float = 1.0, rho0: floa
     return (cp / gamma) * (np.log(p_rel) - gamma * np.log(np.asarray(rho) / rho0))
 
 
+def riemann_star(rho_l, p_l, rho_r, p_r, gamma: float = 1.4, u_l=0.0, u_r=0.0):
+    """Pressure and velocity (p*, u*) of the star region of the exact solution of the ideal-gas Riemann
+    problem with states (rho, u, p) left and right: the root of the pressure function
+    f_L(p) + f_R(p) + u_r - u_l = 0, where f_K is the shock (Rankine-Hugoniot) branch for p > p_K and
+    the rarefaction (isentropic) branch for p <= p_K, found by Newton's method from the mean pressure;
+    u* = (u_l + u_r)/2 + (f_R(p*) - f_L(p*))/2 (Toro, "Riemann Solvers and Numerical Methods for Fluid
+    Dynamics", chapter 4). Vectorised over numpy arrays. A property of the input data (gas dynamics),
+    used to select Riemann problems."""
+    rho_l, p_l, rho_r, p_r = (np.asarray(x, dtype=np.float64) for x in (rho_l, p_l, rho_r, p_r))
+    g = gamma
+
+    def f_and_df(p, rho, pk):
+        ck = np.sqrt(g * pk / rho)
+        a, b = 2.0 / ((g + 1.0) * rho), (g - 1.0) / (g + 1.0) * pk
+        q = np.sqrt(a / (p + b))
+        f_sh = (p - pk) * q
+        df_sh = q * (1.0 - 0.5 * (p - pk) / (p + b))
+        r = (p / pk) ** ((g - 1.0) / (2.0 * g))
+        f_ra = 2.0 * ck / (g - 1.0) * (r - 1.0)
+        df_ra = r / (rho * ck) * (pk / p)
+        shock = p > pk
+        return np.where(shock, f_sh, f_ra), np.where(shock, df_sh, df_ra)
+
+    p = 0.5 * (p_l + p_r)
+    for _ in range(50):
+        fl, dl = f_and_df(p, rho_l, p_l)
+        fr, dr = f_and_df(p, rho_r, p_r)
+        step = (fl + fr + (u_r - u_l)) / (dl + dr)
+        p = np.maximum(p - step, 1e-12 * np.maximum(p_l, p_r))
+        if np.all(np.abs(step) <= 1e-14 * p):
+            break
+    fl, _ = f_and_df(p, rho_l, p_l)
+    fr, _ = f_and_df(p, rho_r, p_r)
+    return p, 0.5 * (u_l + u_r) + 0.5 * (fr - fl)
+
+
+# Flow speed |u| / lambda below which the linearised D1Q3Q3 step around the reference state (rho0, u,
+# s0) of the paper's gas (gamma = 1.4, Pr = 1, c0 = lambda / 2) has spectral radius <= 1, for the free
+# rate s_e = 1.0, 1.1, ..., 1.9 (s_psi coupled, s_eps = 1.5). Values of the stability analysis of the
+# scheme, rounded down to 0.001; the stability tests check each against the oracle's exact Jacobian.
+# Used only to select Riemann data whose flow stays in the stable region.
+STABLE_FLOW_SPEED_S_E = (1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6, 1.7, 1.8, 1.9)
+STABLE_FLOW_SPEED = (0.155, 0.150, 0.144, 0.138, 0.131, 0.123, 0.114, 0.102, 0.087, 0.064)
+
+
 def ragged_batch(B: int, seed: int, p_unit: float, n_min: int = 512, n_max: int = 65536,
                  s_range=(1.0, 1.9), left=(0.8, 1.2), right=(0.3, 0.7), p_bounce: float = 0.5,
-                 entropy_range=None, gamma: float = 1.4) -> RaggedBatch:
+                 entropy_range=None, gamma: float = 1.4, stable_flow: bool = False) -> RaggedBatch:
     """B Riemann problems of uneven lengths: N_b uniform in [n_min, n_max], s_e uniform in
     s_range, left state (rho, p) uniform in ``left``, right state uniform in ``right`` (pressures
     times p_unit), u = 0, split at N_b / 2; boundary periodic or bounce-back with probability
     p_bounce each.
 
     entropy_range = (lo, hi): keep only the draws whose left and right states both have a specific
-    entropy (``entropy_of_state``, c_p = 1) in [lo, hi]. Candidates are drawn from the same
-    distribution in chunks from the same generator and the first B accepted ones are kept, so the
-    result is the conditional distribution of the unfiltered draw."""
+    entropy (``entropy_of_state``, c_p = 1) in [lo, hi]. stable_flow: keep only the draws whose exact
+    Riemann solution moves no faster than STABLE_FLOW_SPEED at their s_e (|u*| from ``riemann_star``,
+    the table interpolated linearly in s_e). Candidates are drawn from the same distribution in chunks
+    from the same generator and the first B accepted ones are kept, so the result is the conditional
+    distribution of the unfiltered draw."""
     rng = np.random.default_rng(np.random.PCG64(seed))
-    if entropy_range is None:
+    if entropy_range is None and not stable_flow:
         lengths = rng.integers(n_min, n_max + 1, B).astype(np.int64)
         s_e = rng.uniform(s_range[0], s_range[1], B)
         states = np.stack([rng.uniform(*left, B), rng.uniform(*left, B),
                            rng.uniform(*right, B), rng.uniform(*right, B)], axis=1)
         bc = (rng.uniform(0, 1, B) < p_bounce).astype(np.int32)
     else:
-        lo, hi = entropy_range
+        lo, hi = entropy_range if entropy_range is not None else (-np.inf, np.inf)
         keep = [[], [], [], []]
         got = 0
         while got < B:
@@ -136,6 +183,9 @@ def ragged_batch(B: int, seed: int, p_unit: float, n_min: int = 512, n_max: int 
             sl = entropy_of_state(st[:, 0], st[:, 1], gamma)
             sr = entropy_of_state(st[:, 2], st[:, 3], gamma)
             ok = (sl >= lo) & (sl <= hi) & (sr >= lo) & (sr <= hi)
+            if stable_flow:
+                _, us = riemann_star(st[:, 0], st[:, 1] * p_unit, st[:, 2], st[:, 3] * p_unit, gamma)
+                ok &= np.abs(us) <= np.interp(se, STABLE_FLOW_SPEED_S_E, STABLE_FLOW_SPEED)
             for lst, arr in zip(keep, (ln, se, st, bb)):
                 lst.append(arr[ok])
             got += int(ok.sum())

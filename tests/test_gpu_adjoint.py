@@ -114,13 +114,19 @@ def test_adjoint_matches_central_differences_of_gpu_forward(lbm):
 
 
 def test_adjoint_fp32_close_to_fp64(lbm):
+    """The FP32 adjoint against the FP64 one, element by element: every component of dL/drho(0) and
+    dL/du(0) within 1e-3 of the largest component of its field (FP32 rounding over the 60 forward and 60
+    reverse steps, amplified by the cancellation in the misfit rho_T - rho*), the rate gradients within
+    1e-3 relative, and the loss within 1e-4."""
     T = 60
     lengths, bc, s_e, data, targets = _case()
     l64, r64, u64, s64 = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T, "f64")
     l32, r32, u32, s32 = _gpu_adjoint(lbm, lengths, bc, s_e, data, targets, T, "f32")
     assert abs(l32 - l64) <= 1e-4 * l64
-    for a, b in ((r32, r64), (u32, u64), (s32, s64)):
-        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+    for name, a, b in (("drho", r32, r64), ("du", u32, u64)):
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err <= 1e-3, (name, err)
+    assert np.all(np.abs(s32 - s64) <= 1e-3 * np.abs(s64)), (s32, s64)
 
 
 def test_autograd_function_matches_adjoint(lbm):

@@ -19,7 +19,8 @@ The restatement must agree with the oracle's exact (dual-number) Jacobian, and b
 stability region of the scheme: stable at rest for -0.15 c_p <= s - s0 <= 0.05 c_p (densities
 0.4-1.2 rho0; up to 0.1 c_p at rho <= rho0) and in slow flow, unstable once s - s0 reaches about 0.15 c_p or |u| about 0.15-0.2 lambda
 (s_e-dependent), and weakly unstable below -0.17 c_p at s_e = 1.9. The ragged Riemann batch whose two
-states both lie in -0.15 c_p <= s - s0 <= 0 then stays stable.
+states both lie in -0.15 c_p <= s - s0 <= 0, and whose exact solution moves no faster than the stable
+flow speed at its s_e, then stays stable.
 """
 import numpy as np
 import pytest
@@ -134,15 +135,34 @@ def test_unstable_from_entropy_above_point_one_five(O):
     assert radius(1.2, 0.0, -0.17, 1.9) > 1.0 + 1e-4
 
 
+@pytest.mark.parametrize("i", range(len(W.STABLE_FLOW_SPEED)))
+def test_stable_flow_speed_table(O, i):
+    """The table of flow speeds the Riemann-data selection uses (W.STABLE_FLOW_SPEED) is the stability
+    limit of the linearised step at the reference state (rho0, u, s0): radius <= 1 at the tabulated
+    speed and > 1 beyond it by 0.002 lambda (the table is the limit rounded down to 0.001), on the restated symbol and on the oracle's Jacobian."""
+    s_e, u = W.STABLE_FLOW_SPEED_S_E[i], W.STABLE_FLOW_SPEED[i]
+    assert radius(1.0, u, 0.0, s_e) <= 1.0 + 1e-12
+    assert radius(1.0, u + 0.002, 0.0, s_e) > 1.0 + 1e-9
+    ph = O.default_phys()
+    for uu, stable in ((u, True), (u + 0.002, False)):
+        B = L.jacobian_blocks(ph, O.coupled_rates(s_e), 1.0, uu, 0.0)
+        rad = max(np.abs(np.linalg.eigvals(L.symbol(B, t))).max() for t in THETAS)
+        assert (rad <= 1.0 + 1e-12) == stable, (s_e, uu, rad)
+
+
 def test_entropy_filtered_riemann_draws_stay_stable(O):
     """Riemann data drawn like the ragged batch but kept only when both states lie in the stable
-    entropy band -0.15 c_p <= s - s0 <= 0 (W.ragged_batch(..., entropy_range=(-0.15, 0.0))): a seeded
-    sample of such lattices (lengths capped for the oracle) runs 2000 steps with no diagnostic flag."""
+    entropy band -0.15 c_p <= s - s0 <= 0 and the exact Riemann solution moves no faster than the
+    stable flow speed of the lattice's s_e (W.ragged_batch(..., entropy_range=(-0.15, 0.0),
+    stable_flow=True)): a seeded sample of such lattices (lengths capped for the oracle) runs 2000
+    steps with no diagnostic flag."""
     ph = O.default_phys()
-    bat = W.ragged_batch(10, 1802, ph.p0, n_min=512, n_max=1024, entropy_range=(-0.15, 0.0))
+    bat = W.ragged_batch(10, 1802, ph.p0, n_min=512, n_max=1024, entropy_range=(-0.15, 0.0), stable_flow=True)
     sl = W.entropy_of_state(bat.states[:, 0], bat.states[:, 1])
     sr = W.entropy_of_state(bat.states[:, 2], bat.states[:, 3])
     assert np.all((sl >= -0.15) & (sl <= 0) & (sr >= -0.15) & (sr <= 0))
+    _, us = W.riemann_star(bat.states[:, 0], bat.states[:, 1] * ph.p0, bat.states[:, 2], bat.states[:, 3] * ph.p0)
+    assert np.all(np.abs(us) <= np.interp(bat.s_e, W.STABLE_FLOW_SPEED_S_E, W.STABLE_FLOW_SPEED))
     for b in range(bat.lengths.size):
         phb = O.default_phys(bc=int(bat.bc[b]))
         r, u, p = bat.lattice(b)
