@@ -177,6 +177,14 @@ int lbm_status(lbm_ctx *ctx);
  * (-1: none). */
 int lbm_debug_persistent(lbm_ctx *ctx, int64_t spin_limit, int64_t withhold_tile);
 
+/* Bounds-checked debug build (the library compiled with -DLBM_DEBUG_BOUNDS, a stand-in for a memory
+ * checker): the step, persistent, double-float and adjoint kernels check every global and shared-memory
+ * index against the extent it must lie in, count and skip an access outside it instead of faulting.
+ * Synchronises the device, then returns in *violations the number of skipped accesses since the last
+ * call (and clears it), with the first bad index and its extent (-1 when none); a build without the
+ * checks returns *violations = -1. LBM_ERR_INVALID_ARG on a null pointer, LBM_ERR_CUDA on a CUDA error. */
+int lbm_debug_bounds(int64_t *violations, int64_t *first_index, int64_t *first_extent);
+
 /* Test hook: applies one of the FP32 functions of the node update elementwise to n floats
  * (device pointers x -> y, enqueued on stream): fn 0 = log(1+x) as evaluated on paired lanes,
  * 1 = log(1+x) on single lanes (CUDA's log1pf), 2 = exp(x)-1 on paired lanes, 3 = exp(x)-1 on

@@ -17,6 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
+# The bounds-checked debug build (-DLBM_DEBUG_BOUNDS): every index of the step, persistent,
+# double-float and adjoint kernels checked before the access; built on demand by its tests.
+DEBUG_OUT_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_OUT_DIR, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "--expt-relaxed-constexpr"]
@@ -40,16 +44,17 @@ def _stale(target: str, sources: list[str]) -> bool:
     return any(os.path.getmtime(s) > t for s in sources)
 
 
-def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, extra_flags: list[str] | None = None, debug_bounds: bool = False) -> str:
+    out_dir, lib = (DEBUG_OUT_DIR, DEBUG_LIB) if debug_bounds else (OUT_DIR, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
-    flags = FLAGS + (extra_flags or [])
+    flags = FLAGS + (extra_flags or []) + (["-DLBM_DEBUG_BOUNDS"] if debug_bounds else [])
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if _stale(o, [s] + deps + [__file__]):
             jobs.append([nvcc] + ARCH + flags + ["-c", s, "-o", o])
@@ -66,11 +71,11 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
         for err in ex.map(run, jobs):
             if verbose and err:
                 print(err, file=sys.stderr)
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

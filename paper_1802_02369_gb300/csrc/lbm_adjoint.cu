@@ -121,23 +121,23 @@ struct NodeFlags {
 template <typename X, int NT>
 __device__ __forceinline__ X left_of(const X* arr, int t, X own) {
   if constexpr (Lane<X>::W == 1) {
-    return t > 0 ? arr[t - 1] : own;
+    return (t > 0 && in_bounds(t - 1, NT)) ? arr[t - 1] : own;
   } else if constexpr (std::is_same<X, df2>::value) {
     const df x0 = df2_get(own, 0);
-    return df2_of(t > 0 ? df2_get(arr[t - 1], 1) : x0, x0);
+    return df2_of((t > 0 && in_bounds(t - 1, NT)) ? df2_get(arr[t - 1], 1) : x0, x0);
   } else {
-    return make_float2(t > 0 ? arr[t - 1].y : own.x, own.x);
+    return make_float2((t > 0 && in_bounds(t - 1, NT)) ? arr[t - 1].y : own.x, own.x);
   }
 }
 template <typename X, int NT>
 __device__ __forceinline__ X right_of(const X* arr, int t, X own) {
   if constexpr (Lane<X>::W == 1) {
-    return t < NT - 1 ? arr[t + 1] : own;
+    return (t < NT - 1 && in_bounds(t + 1, NT)) ? arr[t + 1] : own;
   } else if constexpr (std::is_same<X, df2>::value) {
     const df x1 = df2_get(own, 1);
-    return df2_of(x1, t < NT - 1 ? df2_get(arr[t + 1], 0) : x1);
+    return df2_of(x1, (t < NT - 1 && in_bounds(t + 1, NT)) ? df2_get(arr[t + 1], 0) : x1);
   } else {
-    return make_float2(own.y, t < NT - 1 ? arr[t + 1].x : own.y);
+    return make_float2(own.y, (t < NT - 1 && in_bounds(t + 1, NT)) ? arr[t + 1].x : own.y);
   }
 }
 
@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(NT, std::is_same<X, float2>::value ? 6 : 0) ad
       }
       L = lo;
     }
+    if (!in_bounds(L, B)) continue;
     const LatDev d = lat[L];
     const long long N = d.n, off = d.offset;
     NodeFlags<W> nf;
@@ -377,14 +378,18 @@ __global__ void __launch_bounds__(NT, std::is_same<X, float2>::value ? 6 : 0) ad
     }
 
     // Forward recompute: f(t0 + k) into shared memory, k = 0 .. K - 1.
+    bool lp_ok[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) lp_ok[j] = in_bounds(lp[j], N) && in_bounds(off + lp[j], plane);
     X f[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q)
 #pragma unroll
-      for (int j = 0; j < W; ++j) lset(f[q], j, f0[q * plane + off + lp[j]]);
+      for (int j = 0; j < W; ++j) lset(f[q], j, lp_ok[j] ? f0[q * plane + off + lp[j]] : R(0));
     for (int k = 0; k < K; ++k) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q) sfx[(k * 6 + q) * NT + t] = f[q];
+      for (int q = 0; q < 6; ++q)
+        if (in_bounds((k * 6 + q) * NT + t, K * 6 * NT)) sfx[(k * 6 + q) * NT + t] = f[q];
       if (k == K - 1) break;
       NodeS<X> ms;
       node_state_s(f, c, m_s0h, ms);
@@ -418,11 +423,12 @@ __global__ void __launch_bounds__(NT, std::is_same<X, float2>::value ? 6 : 0) ad
 #pragma unroll
     for (int q = 0; q < 6; ++q)
 #pragma unroll
-      for (int j = 0; j < W; ++j) lset(a[q], j, a_next[q * plane + off + lp[j]]);
+      for (int j = 0; j < W; ++j) lset(a[q], j, lp_ok[j] ? a_next[q * plane + off + lp[j]] : R(0));
     double acc_se = 0.0, acc_sp = 0.0;  // per warp (lane 0), over the K steps
     for (int k = K - 1; k >= 0; --k) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q) f[q] = sfx[(k * 6 + q) * NT + t];
+      for (int q = 0; q < 6; ++q)
+        if (in_bounds((k * 6 + q) * NT + t, K * 6 * NT)) f[q] = sfx[(k * 6 + q) * NT + t];
       X ao[6], gx_se, gx_sp;
       adjoint_node_step<X, NT>(f, a, sh, t, nf, ar, c, ao, gx_se, gx_sp);
 #pragma unroll
@@ -439,12 +445,12 @@ __global__ void __launch_bounds__(NT, std::is_same<X, float2>::value ? 6 : 0) ad
     }
 #pragma unroll
     for (int j = 0; j < W; ++j)
-      if (owned[j])
+      if (owned[j] && in_bounds(pos[j], N) && in_bounds(off + pos[j], plane))
 #pragma unroll
         for (int q = 0; q < 6; ++q) a_out[q * plane + off + pos[j]] = lget(a[q], j);
     if (lane == 0) { sh.sg[0][warp] = acc_se; sh.sg[1][warp] = acc_sp; }
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && in_bounds(tile, ntiles)) {
       double t0 = 0.0, t1 = 0.0;
       for (int w = 0; w < NW; ++w) { t0 += sh.sg[0][w]; t1 += sh.sg[1][w]; }
       grad_tile[2 * tile] += t0;
@@ -674,5 +680,14 @@ template cudaError_t launch_misfit_seed<float>(const float*, const double*, cons
                                                double*, double*, cudaStream_t);
 template cudaError_t launch_misfit_seed<double>(const double*, const double*, const double*, long long, double,
                                                 double*, double*, double*, cudaStream_t);
+
+cudaError_t bounds_record_adjoint(unsigned long long out[3]) {
+#ifdef LBM_DEBUG_BOUNDS
+  return take_bounds_record(out);
+#else
+  out[0] = out[1] = out[2] = 0ULL;
+  return cudaSuccess;
+#endif
+}
 
 }  // namespace lbm

@@ -519,7 +519,7 @@ void rebuild_tables(lbm_ctx* c) {
   }
   c->nchunks = ch;
   for (int ki = 0; ki < 4; ++ki) {
-    const long long bout = (long long)c->NT * c->V - 4 * (1 << ki);
+    const long long bout = lbm::tile_span(c->NT, c->V, c->precision == LBM_F32_SHIFTED) - 4 * (1 << ki);
     long long t = 0;
     for (int b = 0; b < c->B; ++b) {
       LatDev d = c->host_lat[b];
@@ -1045,7 +1045,7 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
   LBM_CK(c, cudaEventCreate(&e0));
   LBM_CK(c, cudaEventCreate(&e1));
   const int Ks[4] = {1, 2, 4, 8};
-  const int NTs[4] = {128, 256, 512, 1024};
+  const int NTs[6] = {32, 64, 128, 256, 512, 1024};
   const int Vs[3] = {1, 2, 4};
   double best = 1e300;
   int bestK = c->K, bestNT = c->NT, bestV = c->V;
@@ -1061,7 +1061,7 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
         int rc = upload_lat(c);
         if (rc) return rc;
         const long long nt_run = std::min(c->ntiles, kTrialTiles);
-        const double nodes = (double)nt_run * (nt * v - 4 * k);
+        const double nodes = (double)nt_run * (lbm::tile_span(nt, v, c->precision == LBM_F32_SHIFTED) - 4 * k);
         float ms = 0.f;
         for (int t = 0; t <= trials; ++t) {  // the first launch is a warm-up
           if (t == 1) LBM_CK(c, cudaEventRecord(e0, c->stream));
@@ -1115,6 +1115,30 @@ int lbm_status(lbm_ctx* c) {
     LBM_CK(c, cudaStreamSynchronize(c->stream));
     return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the persistent kernel expired; the state is not valid");
   }
+  return LBM_OK;
+}
+
+int lbm_debug_bounds(int64_t* violations, int64_t* first_index, int64_t* first_extent) {
+  if (!violations || !first_index || !first_extent) return LBM_ERR_INVALID_ARG;
+#ifdef LBM_DEBUG_BOUNDS
+  if (cudaDeviceSynchronize() != cudaSuccess) return LBM_ERR_CUDA;
+  unsigned long long rec[3][3];
+  if (lbm::bounds_record_step(rec[0]) != cudaSuccess || lbm::bounds_record_df(rec[1]) != cudaSuccess ||
+      lbm::bounds_record_adjoint(rec[2]) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  *violations = 0;
+  *first_index = *first_extent = -1;
+  for (auto& r : rec) {
+    if (r[0] && *violations == 0) {
+      *first_index = (int64_t)r[1];
+      *first_extent = (int64_t)r[2];
+    }
+    *violations += (int64_t)r[0];
+  }
+#else
+  *violations = -1;  // this build has no bounds checks
+  *first_index = *first_extent = -1;
+#endif
   return LBM_OK;
 }
 

@@ -8,6 +8,39 @@
 
 namespace lbm {
 
+// Bounds-checked debug build. Compiled with -DLBM_DEBUG_BOUNDS, the step, persistent, double-float and
+// adjoint kernels check every global and shared-memory index they compute against the extent it must
+// lie in before the access; an index outside is counted, the first one is recorded with its extent,
+// and the access is skipped (a load gives zero), so the kernel runs to its end instead of faulting. The
+// record is per translation unit (take_bounds_record reads and clears it); lbm_debug_bounds gathers
+// them. Without the flag in_bounds is the constant true and the checks compile away.
+#ifdef LBM_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds_rec[3];  // violations, first index, its extent
+static __device__ __noinline__ bool bounds_violation(long long i, long long n) {
+  if (atomicAdd(&g_bounds_rec[0], 1ULL) == 0ULL) {
+    atomicExch(&g_bounds_rec[1], (unsigned long long)i);
+    atomicExch(&g_bounds_rec[2], (unsigned long long)n);
+  }
+  return false;
+}
+__device__ __forceinline__ bool in_bounds(long long i, long long n) {
+  return (i >= 0 && i < n) ? true : bounds_violation(i, n);
+}
+static inline cudaError_t take_bounds_record(unsigned long long out[3]) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_rec, sizeof(unsigned long long) * 3);
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero[3] = {0ULL, 0ULL, 0ULL};
+  return cudaMemcpyToSymbol(g_bounds_rec, zero, sizeof(zero));
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long) { return true; }
+#endif
+// Reads and clears the bounds record of lbm_step.cu, lbm_step_df.cu and lbm_adjoint.cu (zeros when the
+// build has no checks).
+cudaError_t bounds_record_step(unsigned long long out[3]);
+cudaError_t bounds_record_df(unsigned long long out[3]);
+cudaError_t bounds_record_adjoint(unsigned long long out[3]);
+
 // Per-lattice record on the device. tile0 is the index of the lattice's first tile for the current
 // tile width; chunk0 the index of its first diagnostics chunk.
 struct LatDev {
@@ -390,6 +423,14 @@ inline const Consts<float>& ConstSet<float>::get<float>() const { return s; }
 template <>
 template <>
 inline const Consts<float2>& ConstSet<float>::get<float2>() const { return p; }
+
+// Nodes a tile of NT threads x V nodes spans: NT V, less the ghost nodes that the warps of an FP32 tile
+// of four nodes per thread share (kGhost per warp edge, see tile_body_packed). A tile stores
+// tile_span - 4K of them (the halo of K steps is 2K nodes per side).
+constexpr int kGhost = 4;
+__host__ __device__ constexpr long long tile_span(int NT, int V, bool f32) {
+  return (long long)NT * V - ((f32 && V == 4) ? 2LL * kGhost * (NT / 32 - 1) : 0LL);
+}
 
 // Host-side launchers (lbm_step.cu). A tile has NT threads of V nodes; K steps per launch.
 // Only the first ntiles tiles are processed (the autotuner times partial launches).

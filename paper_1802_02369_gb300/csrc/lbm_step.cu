@@ -11,87 +11,18 @@
 // thread's registers, from the adjacent lane (warp shuffle) or, at warp edges, from two words of
 // shared memory per warp. After the collision every node pulls its incoming moving populations
 // (f+, g+ from the left, f-, g- from the right) the same way. f0 and g0 never move. A wall node
-// (bounce-back) takes its own reflected population instead. Two CTA barriers per step.
+// (bounce-back) takes its own reflected population instead. Two CTA barriers per step (none in a
+// one-warp tile, whose edges are the tile halo).
 #include <type_traits>
 
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
-template <typename R, bool CG>
-__device__ __forceinline__ R ld_state(const R* p) {
-  if constexpr (CG) return __ldcg(p);  // L2 only: the persistent kernel reads data other CTAs wrote
-  else return *p;
-}
-
-// Loads (or stores) the six planes of a tile with fully coalesced accesses through a shared buffer of
-// NT*V elements, one plane at a time; thread t then holds (or held) nodes tV .. tV + V - 1. Used by the
-// persistent kernel, whose loads bypass L1 (other CTAs rewrite the buffers during the launch).
-// Planes staged per barrier pair: all six when they fit in 24 KB, else one at a time.
-template <typename R, int NT, int V>
-struct StagePlanes {
-  static constexpr int value = (6 * NT * V * (int)sizeof(R) <= 24576) ? 6 : 1;
-};
-
-template <typename R, int NT, int V, bool CG, bool WALLS>
-__device__ __forceinline__ void staged_load(const R* in, long long plane, long long off, long long N, long long p_first,
-                                            R* stage, R (&f)[V][6]) {
-  constexpr int PL = StagePlanes<R, NT, V>::value;
-  long long src[V];
-#pragma unroll
-  for (int q = 0; q < V; ++q) {
-    long long lp = p_first + q * NT + threadIdx.x;
-    if (!WALLS) {
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-    } else {
-      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
-    }
-    src[q] = off + lp;
-  }
-#pragma unroll
-  for (int i0 = 0; i0 < 6; i0 += PL) {
-#pragma unroll
-    for (int p = 0; p < PL; ++p)
-#pragma unroll
-      for (int q = 0; q < V; ++q)
-        stage[p * NT * V + q * NT + threadIdx.x] = ld_state<R, CG>(in + (i0 + p) * plane + src[q]);
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PL; ++p)
-#pragma unroll
-      for (int v = 0; v < V; ++v) f[v][i0 + p] = stage[p * NT * V + threadIdx.x * V + v];
-    __syncthreads();
-  }
-}
-
-template <typename R, int NT, int V>
-__device__ __forceinline__ void staged_store(R* out, long long plane, long long off, long long N, long long p_first,
-                                             int halo, int bout, R* stage, const R (&f)[V][6]) {
-  constexpr int PL = StagePlanes<R, NT, V>::value;
-#pragma unroll
-  for (int i0 = 0; i0 < 6; i0 += PL) {
-#pragma unroll
-    for (int p = 0; p < PL; ++p)
-#pragma unroll
-      for (int v = 0; v < V; ++v) stage[p * NT * V + threadIdx.x * V + v] = f[v][i0 + p];
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PL; ++p)
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int n = q * NT + threadIdx.x;
-        const long long pos = p_first + n;
-        if (n >= halo && n < halo + bout && pos < N) out[(i0 + p) * plane + off + pos] = stage[p * NT * V + n];
-      }
-    __syncthreads();
-  }
-}
-
-// Advances one tile K steps: reads `in`, writes the interior of the tile to `out`. With a shared
-// staging buffer (persistent kernel) the global accesses are coalesced through it.
-template <typename R, int NT, int V, bool CG, bool WALLS>
+// Advances one tile K steps: reads `in`, writes the interior of the tile to `out`.
+template <typename R, int NT, int V, bool WALLS>
 __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, const LatDev& d, long long start,
-                                          int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4], R* stage) {
+                                          int K, const Consts<R>& c, R (*e_ut)[4], R (*e_f)[4]) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int halo = 2 * K;
@@ -111,21 +42,18 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
   }
-  if (stage) {
-    staged_load<R, NT, V, CG, WALLS>(in, plane, off, N, start - halo, stage, f);
-  } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      long long lp = pos0 + v;
-      if (!WALLS) {
-        if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-      } else {
-        lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
-      }
-      const R* src = in + off + lp;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) f[v][i] = ld_state<R, CG>(src + i * plane);
+  for (int v = 0; v < V; ++v) {
+    long long lp = pos0 + v;
+    if (!WALLS) {
+      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+    } else {
+      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
+    const R* src = in + off + lp;
+    const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) f[v][i] = ok ? src[i * plane] : R{};
   }
 
   for (int k = 0; k < K; ++k) {
@@ -135,11 +63,13 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     // u' and theta of the neighbours of the first and last node of this thread.
     R uL = __shfl_up_sync(0xffffffffu, m[V - 1].u, 1), TL = __shfl_up_sync(0xffffffffu, m[V - 1].th, 1);
     R uR = __shfl_down_sync(0xffffffffu, m[0].u, 1), TR = __shfl_down_sync(0xffffffffu, m[0].th, 1);
-    if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].th; }
-    if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].th; }
-    __syncthreads();
-    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    if constexpr (NW > 1) {  // a one-warp tile has no warp edge inside it
+      if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].th; }
+      if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].th; }
+      __syncthreads();
+      if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+      if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    }
     // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
 
     R fs[V][6];
@@ -154,11 +84,13 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     // (viii) streaming: pull f+, g+ from the left neighbour and f-, g- from the right one.
     R fpL = __shfl_up_sync(0xffffffffu, fs[V - 1][1], 1), gpL = __shfl_up_sync(0xffffffffu, fs[V - 1][4], 1);
     R fmR = __shfl_down_sync(0xffffffffu, fs[0][2], 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5], 1);
-    if (lane == 31) { e_f[warp][0] = fs[V - 1][1]; e_f[warp][1] = fs[V - 1][4]; }
-    if (lane == 0) { e_f[warp][2] = fs[0][2]; e_f[warp][3] = fs[0][5]; }
-    __syncthreads();
-    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    if constexpr (NW > 1) {
+      if (lane == 31) { e_f[warp][0] = fs[V - 1][1]; e_f[warp][1] = fs[V - 1][4]; }
+      if (lane == 0) { e_f[warp][2] = fs[0][2]; e_f[warp][3] = fs[0][5]; }
+      __syncthreads();
+      if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+      if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       f[v][0] = fs[v][0];
@@ -170,15 +102,11 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
     }
   }
 
-  if (stage) {
-    staged_store<R, NT, V>(out, plane, off, N, start - halo, halo, bout, stage, f);
-    return;
-  }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int local = threadIdx.x * V + v;
     const long long pos = pos0 + v;
-    if (local >= halo && local < halo + bout && pos < N) {
+    if (local >= halo && local < halo + bout && pos < N && in_bounds(pos, N) && in_bounds(off + pos, plane)) {
       R* dst = out + off + pos;
 #pragma unroll
       for (int i = 0; i < 6; ++i) dst[i * plane] = f[v][i];
@@ -191,22 +119,37 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 // of a thread holds nodes l (x) and l + NL (y): the left neighbours of lane l > 0 are then exactly
 // lane l - 1 and the right neighbours of lane l < NL - 1 exactly lane l + 1, so only the two outer
 // lanes assemble a neighbour pair from two registers.
-template <int NT, int V, bool CG, bool WALLS, bool FULL>
+//
+// With four nodes per thread (GHOST) the warps of a tile overlap instead of exchanging their edges
+// every step: warp w holds the 128 nodes starting at w * (128 - 2G), the first and last G = 4 of which
+// are ghost copies of the neighbouring warps' nodes. A warp steps on shuffles alone; its outer G nodes
+// lose validity at 2 nodes per step (the step's dependency radius), and every P = G / 2 steps they are
+// refreshed from the neighbours' valid nodes (lane 30 of warp w - 1 and lane 1 of warp w + 1) through
+// shared memory, behind one CTA barrier: K/P - 1 barriers per tile instead of two per step, for
+// 2G / 128 = 6 % more node updates. A tile then spans kTileSpan(NT, V) = NT V - 2G (NT/32 - 1) nodes.
+template <int NT, int V, bool WALLS, bool FULL>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
-                                                 float (*e_ut)[4], float (*e_f)[4], float* stage) {
+                                                 float (*e_ut)[4], float (*e_f)[4], float2* gbuf) {
   constexpr int NW = NT / 32, NL = V / 2;
+  constexpr bool GHOST = V == 4 && NW > 1;
+  constexpr int G = kGhost, P = kGhost / 2, WS = 32 * V - 2 * G;  // ghosts per side, refresh period, warp stride
+  constexpr int SPAN = (int)tile_span(NT, V, true);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int halo = 2 * K;
-  const int bout = NT * V - 2 * halo;
+  const int bout = SPAN - 2 * halo;
   const long long off = d.offset, N = d.n;
-  const StepParams<float> P = step_params(d, 0.0f);
-  const float2 s_e = make_float2(P.s_e, P.s_e), s_psi = make_float2(P.s_psi, P.s_psi);
-  const float2 s_eps = make_float2(P.s_eps, P.s_eps), q_src = make_float2(P.q_src, P.q_src);
-  const float2 s0h = make_float2(P.s0h, P.s0h), m_s0h = make_float2(-P.s0h, -P.s0h);
-  const float2 le0 = make_float2(P.lin_e0, P.lin_e0), lp0 = make_float2(P.lin_p0, P.lin_p0);
-  const float2 lq0 = make_float2(P.lin_q0, P.lin_q0);
-  const long long pos0 = start - halo + (long long)threadIdx.x * V;
+  const StepParams<float> P_ = step_params(d, 0.0f);
+  const float2 s_e = make_float2(P_.s_e, P_.s_e), s_psi = make_float2(P_.s_psi, P_.s_psi);
+  const float2 s_eps = make_float2(P_.s_eps, P_.s_eps), q_src = make_float2(P_.q_src, P_.q_src);
+  const float2 s0h = make_float2(P_.s0h, P_.s0h), m_s0h = make_float2(-P_.s0h, -P_.s0h);
+  const float2 le0 = make_float2(P_.lin_e0, P_.lin_e0), lp0 = make_float2(P_.lin_p0, P_.lin_p0);
+  const float2 lq0 = make_float2(P_.lin_q0, P_.lin_q0);
+  // First node of this thread within the tile span.
+  const int local0 = GHOST ? warp * WS + lane * V : (int)threadIdx.x * V;
+  const long long pos0 = start - halo + local0;
+  // Ghost nodes of a warp that has a neighbour on that side: neither refreshed nor stored by this warp.
+  const bool ghost_lane = GHOST && ((lane == 0 && warp > 0) || (lane == 31 && warp < NW - 1));
 
   // Node v of the thread sits in lane v % NL, half v / NL.
   float2 f[NL][6];
@@ -217,14 +160,7 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
   }
-  if (stage) {
-    float fl[V][6];
-    staged_load<float, NT, V, CG, WALLS>(in, plane, off, N, start - halo, stage, fl);
-#pragma unroll
-    for (int l = 0; l < NL; ++l)
-#pragma unroll
-      for (int i = 0; i < 6; ++i) f[l][i] = make_float2(fl[l][i], fl[l + NL][i]);
-  } else {
+  {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       long long lp = pos0 + v;
@@ -234,28 +170,72 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
         lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
       }
       const float* src = in + off + lp;
+      const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        const float x = ld_state<float, CG>(src + i * plane);
+        const float x = ok ? src[i * plane] : 0.0f;
         if (v >= NL) f[v - NL][i].y = x; else f[v][i].x = x;
       }
     }
   }
 
+  // Ghost exchange buffer gbuf (GS float2 slots), alternating by refresh: [side][parity][warp][lane of the
+  // thread][population], side 0 = lane 30's nodes for warp + 1, side 1 = lane 1's nodes for warp - 1.
+  const auto gslot = [&](int side, int par, int w, int l, int i) { return (((side * 2 + par) * NW + w) * NL + l) * 6 + i; };
+  constexpr int GS = GHOST ? 2 * 2 * NW * NL * 6 : 1;
+
   for (int k = 0; k < K; ++k) {
+    if constexpr (GHOST) {
+      if (k > 0 && k % P == 0) {
+        const int par = (k / P) & 1;
+        if (lane == 30 && warp < NW - 1) {
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+              if (in_bounds(gslot(0, par, warp, l, i), GS)) gbuf[gslot(0, par, warp, l, i)] = f[l][i];
+        }
+        if (lane == 1 && warp > 0) {
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+              if (in_bounds(gslot(1, par, warp, l, i), GS)) gbuf[gslot(1, par, warp, l, i)] = f[l][i];
+        }
+        __syncthreads();
+        if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) {
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+              if (in_bounds(gslot(0, par, warp - 1, l, i), GS)) f[l][i] = gbuf[gslot(0, par, warp - 1, l, i)];
+        }
+        if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) {
+#pragma unroll
+          for (int l = 0; l < NL; ++l)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+              if (in_bounds(gslot(1, par, warp + 1, l, i), GS)) f[l][i] = gbuf[gslot(1, par, warp + 1, l, i)];
+        }
+      }
+    }
     NodeS<float2> m[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {  // series first; a pair with a node outside their ranges is redone
       if (!node_state_s<float2, true, FULL>(f[l], c, m_s0h, m[l])) node_state_s<float2, false, FULL>(f[l], c, m_s0h, m[l]);
     }
-    // Node V - 1 is lane NL - 1, half y; node 0 is lane 0, half x.
+    // Node V - 1 is lane NL - 1, half y; node 0 is lane 0, half x. (At the outer edges of a warp these
+    // are stand-ins: in a ghost tile those nodes are ghosts, refreshed before they are needed; otherwise
+    // they come from the neighbouring warp below, or they lie in the tile halo and are never stored.)
     float uL = __shfl_up_sync(0xffffffffu, m[NL - 1].u.y, 1), TL = __shfl_up_sync(0xffffffffu, m[NL - 1].th.y, 1);
     float uR = __shfl_down_sync(0xffffffffu, m[0].u.x, 1), TR = __shfl_down_sync(0xffffffffu, m[0].th.x, 1);
-    if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].th.y; }
-    if (lane == 0) { e_ut[warp][2] = m[0].u.x; e_ut[warp][3] = m[0].th.x; }
-    __syncthreads();
-    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    if constexpr (NW > 1 && !GHOST) {
+      if (lane == 31) { e_ut[warp][0] = m[NL - 1].u.y; e_ut[warp][1] = m[NL - 1].th.y; }
+      if (lane == 0) { e_ut[warp][2] = m[0].u.x; e_ut[warp][3] = m[0].th.x; }
+      __syncthreads();
+      if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+      if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    }
 
     float2 fs[NL][6];
 #pragma unroll
@@ -272,11 +252,13 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     }
     float fpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][1].y, 1), gpL = __shfl_up_sync(0xffffffffu, fs[NL - 1][4].y, 1);
     float fmR = __shfl_down_sync(0xffffffffu, fs[0][2].x, 1), gmR = __shfl_down_sync(0xffffffffu, fs[0][5].x, 1);
-    if (lane == 31) { e_f[warp][0] = fs[NL - 1][1].y; e_f[warp][1] = fs[NL - 1][4].y; }
-    if (lane == 0) { e_f[warp][2] = fs[0][2].x; e_f[warp][3] = fs[0][5].x; }
-    __syncthreads();
-    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    if constexpr (NW > 1 && !GHOST) {
+      if (lane == 31) { e_f[warp][0] = fs[NL - 1][1].y; e_f[warp][1] = fs[NL - 1][4].y; }
+      if (lane == 0) { e_f[warp][2] = fs[0][2].x; e_f[warp][3] = fs[0][5].x; }
+      __syncthreads();
+      if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+      if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       // f+, g+ from the left node; f-, g- from the right node; walls reflect their own.
@@ -297,20 +279,12 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     }
   }
 
-  if (stage) {
-    float fl[V][6];
-#pragma unroll
-    for (int v = 0; v < V; ++v)
-#pragma unroll
-      for (int i = 0; i < 6; ++i) fl[v][i] = v >= NL ? f[v - NL][i].y : f[v][i].x;
-    staged_store<float, NT, V>(out, plane, off, N, start - halo, halo, bout, stage, fl);
-    return;
-  }
+  if (ghost_lane) return;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int local = threadIdx.x * V + v;
+    const int local = local0 + v;
     const long long pos = pos0 + v;
-    if (local >= halo && local < halo + bout && pos < N) {
+    if (local >= halo && local < halo + bout && pos < N && in_bounds(pos, N) && in_bounds(off + pos, plane)) {
       float* dst = out + off + pos;
 #pragma unroll
       for (int i = 0; i < 6; ++i) dst[i * plane] = v >= NL ? f[v - NL][i].y : f[v][i].x;
@@ -341,24 +315,30 @@ struct Lanes<float, 4> {
   using type = float2;
 };
 
-template <typename R, int NT, int V, bool CG>
+// float2 slots of the ghost exchange buffer of a tile (tile_body_packed), at least one.
+template <typename R, int NT, int V>
+struct GhostSlots {
+  static constexpr int value = (sizeof(R) == 4 && V == 4 && NT > 32) ? 2 * 2 * (NT / 32) * (V / 2) * 6 : 1;
+};
+
+template <typename R, int NT, int V>
 __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                             int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
-                                            R (*e_f)[4], R* stage = nullptr) {
+                                            R (*e_f)[4], float2* gbuf) {
   // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
   if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
     // The paper's scheme (nonlinear equilibria, entropy source) without per-node mode tests.
     const bool full = c.eq_mode == 0 && c.source_on;
     if (d.bc == 0) {
-      if (full) tile_body_packed<NT, V, CG, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
-      else tile_body_packed<NT, V, CG, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+      if (full) tile_body_packed<NT, V, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
+      else tile_body_packed<NT, V, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
     } else {
-      if (full) tile_body_packed<NT, V, CG, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
-      else tile_body_packed<NT, V, CG, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+      if (full) tile_body_packed<NT, V, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
+      else tile_body_packed<NT, V, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
     }
   } else {
-    if (d.bc == 0) tile_body<R, NT, V, CG, false>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
-    else tile_body<R, NT, V, CG, true>(in, out, plane, d, start, K, c, e_ut, e_f, stage);
+    if (d.bc == 0) tile_body<R, NT, V, false>(in, out, plane, d, start, K, c, e_ut, e_f);
+    else tile_body<R, NT, V, true>(in, out, plane, d, start, K, c, e_ut, e_f);
   }
 }
 
@@ -374,21 +354,39 @@ cudaError_t launch_tile_map(const LatDev* lat, int B, long long ntiles, int* map
   return cudaGetLastError();
 }
 
-// 128 threads of four FP32 nodes: at least eight resident CTAs per SM, i.e. at most 64 registers
-// (measured faster than the 80-90 the compiler picks otherwise). A minimum of 0 leaves the other
-// instances to the compiler's own choice (an explicit 1 lets it take far more registers).
+// Minimum resident CTAs per SM for __launch_bounds__. 128 threads of four FP32 nodes: eight, i.e. at
+// most 64 registers (measured faster than the 80-90 the compiler picks otherwise); one-warp tiles of
+// four nodes likewise 32 warps per SM. A minimum of 0 leaves the other instances to the compiler's own
+// choice (an explicit 1 lets it take far more registers).
+#ifndef LBM_MINCTAS_F32_128x4
+#define LBM_MINCTAS_F32_128x4 8
+#endif
+#ifndef LBM_MINCTAS_F32_64x4
+#define LBM_MINCTAS_F32_64x4 0
+#endif
 template <typename R, int NT, int V>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 8 : 0) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
+struct MinCtas {
+  static constexpr int value = sizeof(R) != 4 ? 0
+                               : (NT == 128 && V == 4) ? LBM_MINCTAS_F32_128x4
+                               : (NT == 64 && V == 4) ? LBM_MINCTAS_F32_64x4
+                               : (NT == 32 && V == 4) ? 32
+                               : 0;
+};
+
+template <typename R, int NT, int V>
+__global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) step_tiles_kernel(const R* __restrict__ in, R* __restrict__ out,
                                                         long long plane, const LatDev* __restrict__ lat,
                                                         const int* __restrict__ tile_lat, int B, long long ntiles,
                                                         int K, Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
-  const long long bout = NT * V - 4 * K;
+  __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
+  const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
+    if (!in_bounds(L, B)) continue;
     const LatDev d = lat[L];
-    tile_update<R, NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
+    tile_update<R, NT, V>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f, gbuf);
   }
 }
 
@@ -413,7 +411,10 @@ cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev
   LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
   LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
   LBM_CASE(1024, 1)
-  if constexpr (sizeof(R) == 4) { LBM_CASE(1024, 2) }
+  if constexpr (sizeof(R) == 4) {
+    LBM_CASE(1024, 2)
+    LBM_CASE(32, 4) LBM_CASE(64, 4)
+  }
 #undef LBM_CASE
   return cudaErrorInvalidValue;
 }
@@ -438,19 +439,20 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 }
 
 template <typename R, int NT, int V>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 8 : 0) persistent_kernel(R* buf0, R* buf1, long long plane,
+__global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kernel(R* buf0, R* buf1, long long plane,
                                                         const LatDev* __restrict__ lat,
                                                         const int* __restrict__ tile_lat, int B, long long ntiles,
                                                         int K, long long nblocks, PersistentCtl ctl,
                                                         Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
-  __shared__ R stage[StagePlanes<R, NT, V>::value * NT * V];
+  __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
   __shared__ long long s_next;
   __shared__ int s_go;
-  const long long nunits = (ntiles + kUnitTiles - 1) / kUnitTiles;
+  constexpr int U = kUnitTiles;  // tiles per work unit
+  const long long nunits = (ntiles + U - 1) / U;
   const long long total = nblocks * nunits;
-  const long long bout = NT * V - 4 * K;
+  const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
   if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);
   __syncthreads();
   for (;;) {
@@ -460,26 +462,29 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 
     const long long b = u / nunits, k = u % nunits;
     if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);  // claim ahead
     if (threadIdx.x < 32) {
-      // Lane l checks tile k * kUnitTiles + l: its own unit and the units of its lattice neighbours
+      // Lane l checks tile k * U + l: its own unit and the units of its lattice neighbours
       // must have finished block b - 1.
       // Every exit of this loop is warp-uniform: the status word is read by lane 0 and broadcast.
       int go = __shfl_sync(0xffffffffu, threadIdx.x == 0 ? *((volatile int*)ctl.status) : 0, 0) == 0;
       if (go && b > 0) {
         long long uL = k, uR = k;
-        const long long i = k * kUnitTiles + threadIdx.x;
-        if (threadIdx.x < kUnitTiles && i < ntiles) {
-          const int L = B > 1 ? tile_lat[i] : 0;
+        const long long i = k * U + threadIdx.x;
+        if ((int)threadIdx.x < U && i < ntiles && in_bounds(i, ntiles)) {
+          int L = B > 1 ? tile_lat[i] : 0;
+          if (!in_bounds(L, B)) L = 0;
           const long long t0 = lat[L].tile0;
           const long long nt = (L + 1 < B ? lat[L + 1].tile0 : ntiles) - t0;
           const bool periodic = lat[L].bc == 0;
           const long long left = i > t0 ? i - 1 : (periodic ? t0 + nt - 1 : i);
           const long long right = i < t0 + nt - 1 ? i + 1 : (periodic ? t0 : i);
-          uL = left / kUnitTiles;
-          uR = right / kUnitTiles;
+          uL = left / U;
+          uR = right / U;
         }
         long long spins = 0;
+        long long uk = k;
+        if (!in_bounds(uk, nunits) || !in_bounds(uL, nunits) || !in_bounds(uR, nunits)) uL = uR = uk = 0;
         for (;;) {
-          const bool ready = ld_acquire_gpu(ctl.done + k) >= b && ld_acquire_gpu(ctl.done + uL) >= b &&
+          const bool ready = ld_acquire_gpu(ctl.done + uk) >= b && ld_acquire_gpu(ctl.done + uL) >= b &&
                              ld_acquire_gpu(ctl.done + uR) >= b;
           if (__all_sync(0xffffffffu, ready)) break;
           const int st = __shfl_sync(0xffffffffu, threadIdx.x == 0 ? *((volatile int*)ctl.status) : 0, 0);
@@ -491,6 +496,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 
           }
           __nanosleep(100);
         }
+        // The acquire loads above, this fence and the CTA barrier below order every thread's later
+        // (ordinary, L1-cached) loads of the tiles after the neighbours' released writes.
+        __threadfence();
       }
       if (threadIdx.x == 0) s_go = go;
     }
@@ -500,14 +508,15 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 128 && V == 4) ? 
     if (!withheld) {
       R* in = (b & 1) ? buf1 : buf0;
       R* out = (b & 1) ? buf0 : buf1;
-      for (long long i = k * kUnitTiles; i < (k + 1) * kUnitTiles && i < ntiles; ++i) {
+      for (long long i = k * U; i < (k + 1) * U && i < ntiles; ++i) {
         const int L = B > 1 ? tile_lat[i] : 0;
+        if (!in_bounds(L, B)) continue;
         const LatDev d = lat[L];
-        tile_update<R, NT, V, true>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, stage);
+        tile_update<R, NT, V>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, gbuf);
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !withheld) {
+    if (threadIdx.x == 0 && !withheld && in_bounds(k, nunits)) {
       __threadfence();
       st_release_gpu(ctl.done + k, (int)(b + 1));
     }
@@ -543,7 +552,10 @@ cudaError_t launch_persistent(R* buf0, R* buf1, long long plane, const LatDev* l
   LBM_CASE(256, 1) LBM_CASE(256, 2) LBM_CASE(256, 4)
   LBM_CASE(512, 1) LBM_CASE(512, 2) LBM_CASE(512, 4)
   LBM_CASE(1024, 1)
-  if constexpr (sizeof(R) == 4) { LBM_CASE(1024, 2) }
+  if constexpr (sizeof(R) == 4) {
+    LBM_CASE(1024, 2)
+    LBM_CASE(32, 4) LBM_CASE(64, 4)
+  }
 #undef LBM_CASE
   return cudaErrorInvalidValue;
 }
@@ -555,13 +567,25 @@ template cudaError_t launch_persistent<double>(double*, double*, long long, cons
                                                int, int, int, long long, const PersistentCtl&,
                                                const ConstSet<double>&, cudaStream_t);
 
+cudaError_t bounds_record_step(unsigned long long out[3]) {
+#ifdef LBM_DEBUG_BOUNDS
+  return take_bounds_record(out);
+#else
+  out[0] = out[1] = out[2] = 0ULL;
+  return cudaSuccess;
+#endif
+}
+
 bool valid_tile_config(int K, int NT, int V, bool fp64) {
   const bool nt_ok = NT == 128 || NT == 256 || NT == 512 || NT == 1024;
   const bool v_ok = V == 1 || V == 2 || V == 4;
   const bool k_ok = K == 1 || K == 2 || K == 4 || K == 8;
   // 1024 x 4 is not instantiated; FP64 1024 x 2 would spill at the 64-register cap of 1024 threads.
   const bool size_ok = !(NT == 1024 && V == 4) && !(fp64 && NT == 1024 && V == 2);
-  return nt_ok && v_ok && k_ok && size_ok && NT * V - 4 * K >= 32;
+  // FP32 only: one-warp and two-warp tiles of four nodes per thread (one-warp tiles exchange nothing
+  // through shared memory and need no CTA barrier).
+  const bool f32_extra = !fp64 && k_ok && V == 4 && (NT == 32 || NT == 64);
+  return ((nt_ok && v_ok && k_ok && size_ok) || f32_extra) && tile_span(NT, V, !fp64) - 4 * K >= 32;
 }
 
 template cudaError_t launch_step_tiles<float>(const float*, float*, long long, const LatDev*, const int*, int,

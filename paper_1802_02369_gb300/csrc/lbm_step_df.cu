@@ -52,8 +52,9 @@ __device__ __forceinline__ void tile_body_df(const double* __restrict__ in, doub
       lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
     const double* src = in + off + lp;
+    const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) f[v][i] = to_df(src[i * plane]);
+    for (int i = 0; i < 6; ++i) f[v][i] = to_df(ok ? src[i * plane] : 0.0);
   }
 
   for (int k = 0; k < K; ++k) {
@@ -65,8 +66,8 @@ __device__ __forceinline__ void tile_body_df(const double* __restrict__ in, doub
     if (lane == 31) { e_ut[warp][0] = m[V - 1].u; e_ut[warp][1] = m[V - 1].th; }
     if (lane == 0) { e_ut[warp][2] = m[0].u; e_ut[warp][3] = m[0].th; }
     __syncthreads();
-    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
     // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
 
     df fs[V][6];
@@ -84,8 +85,8 @@ __device__ __forceinline__ void tile_body_df(const double* __restrict__ in, doub
     if (lane == 31) { e_f[warp][0] = fs[V - 1][1]; e_f[warp][1] = fs[V - 1][4]; }
     if (lane == 0) { e_f[warp][2] = fs[0][2]; e_f[warp][3] = fs[0][5]; }
     __syncthreads();
-    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       f[v][0] = fs[v][0];
@@ -101,7 +102,7 @@ __device__ __forceinline__ void tile_body_df(const double* __restrict__ in, doub
   for (int v = 0; v < V; ++v) {
     const int local = threadIdx.x * V + v;
     const long long pos = pos0 + v;
-    if (local >= halo && local < halo + bout && pos < N) {
+    if (local >= halo && local < halo + bout && pos < N && in_bounds(pos, N) && in_bounds(off + pos, plane)) {
       double* dst = out + off + pos;
 #pragma unroll
       for (int i = 0; i < 6; ++i) dst[i * plane] = to_double(f[v][i]);
@@ -142,8 +143,9 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
       lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
     }
     const double* src = in + off + lp;
+    const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) df2_set(f[v >> 1][i], v & 1, to_df(src[i * plane]));
+    for (int i = 0; i < 6; ++i) df2_set(f[v >> 1][i], v & 1, to_df(ok ? src[i * plane] : 0.0));
   }
 
   for (int k = 0; k < K; ++k) {
@@ -155,8 +157,8 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
     if (lane == 31) { e_ut[warp][0] = df2_get(m[NL - 1].u, 1); e_ut[warp][1] = df2_get(m[NL - 1].th, 1); }
     if (lane == 0) { e_ut[warp][2] = df2_get(m[0].u, 0); e_ut[warp][3] = df2_get(m[0].th, 0); }
     __syncthreads();
-    if (lane == 0 && warp > 0) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
+    if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { uL = e_ut[warp - 1][0]; TL = e_ut[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { uR = e_ut[warp + 1][2]; TR = e_ut[warp + 1][3]; }
     // (In the outermost nodes of the tile these are stand-ins; those nodes are never stored.)
 
     df2 fs[NL][6];
@@ -180,8 +182,8 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
     if (lane == 31) { e_f[warp][0] = df2_get(fs[NL - 1][1], 1); e_f[warp][1] = df2_get(fs[NL - 1][4], 1); }
     if (lane == 0) { e_f[warp][2] = df2_get(fs[0][2], 0); e_f[warp][3] = df2_get(fs[0][5], 0); }
     __syncthreads();
-    if (lane == 0 && warp > 0) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
-    if (lane == 31 && warp < NW - 1) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
+    if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) { fpL = e_f[warp - 1][0]; gpL = e_f[warp - 1][1]; }
+    if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) { fmR = e_f[warp + 1][2]; gmR = e_f[warp + 1][3]; }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
       f[l][0] = fs[l][0];
@@ -200,7 +202,7 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
   for (int v = 0; v < V; ++v) {
     const int local = threadIdx.x * V + v;
     const long long pos = pos0 + v;
-    if (local >= halo && local < halo + bout && pos < N) {
+    if (local >= halo && local < halo + bout && pos < N && in_bounds(pos, N) && in_bounds(off + pos, plane)) {
       double* dst = out + off + pos;
 #pragma unroll
       for (int i = 0; i < 6; ++i) dst[i * plane] = to_double(df2_get(f[v >> 1][i], v & 1));
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(NT) step_tiles_df2_kernel(const double* __rest
   const long long bout = NT * V - 4 * K;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
+    if (!in_bounds(L, B)) continue;
     const LatDev d = lat[L];
     if (d.bc == 0) tile_body_df2<NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
     else tile_body_df2<NT, V, true>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(NT) step_tiles_df_kernel(const double* __restr
   const long long bout = NT * V - 4 * K;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
+    if (!in_bounds(L, B)) continue;
     const LatDev d = lat[L];
     if (d.bc == 0) tile_body_df<NT, V, false>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
     else tile_body_df<NT, V, true>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f);
@@ -255,6 +259,15 @@ cudaError_t launch_df_nt_v(const double* in, double* out, long long plane, const
 }
 
 }  // namespace
+
+cudaError_t bounds_record_df(unsigned long long out[3]) {
+#ifdef LBM_DEBUG_BOUNDS
+  return take_bounds_record(out);
+#else
+  out[0] = out[1] = out[2] = 0ULL;
+  return cudaSuccess;
+#endif
+}
 
 bool valid_df_config(int K, int NT, int V) {
   const bool nt_ok = NT == 128 || NT == 256 || NT == 512;

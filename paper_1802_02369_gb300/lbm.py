@@ -18,7 +18,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
+# LBM_LIBRARY selects another build of the same library (the bounds-checked debug build of the tests).
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(HERE, "_build", "liblbm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "lbm.h")
 
 LBM_OK = 0
@@ -129,6 +130,7 @@ def load_library(path: str = LIB_PATH):
             "lbm_adjoint_get_config": (i32, [vp, P(i32)]),
             "lbm_status": (i32, [vp]),
             "lbm_debug_persistent": (i32, [vp, i64, i64]),
+            "lbm_debug_bounds": (i32, [P(i64), P(i64), P(i64)]),
             "lbm_fd_create": (i32, [P(vp), i64, d, d, d, i32, P(lbm_phys), vp]),
             "lbm_fd_destroy": (None, [vp]),
             "lbm_fd_last_error": (ctypes.c_char_p, [vp]),
@@ -194,6 +196,17 @@ def install_torch_allocator():
     rc = lib.lbm_set_allocator(a, f, None)
     if rc != LBM_OK:
         raise LbmError(rc, "lbm_set_allocator failed")
+
+
+def debug_bounds():
+    """(violations, first index, its extent) of the bounds-checked debug build since the last call;
+    violations = -1 for a build without the checks (lbm_debug_bounds)."""
+    lib = load_library()
+    v, i, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.lbm_debug_bounds(ctypes.byref(v), ctypes.byref(i), ctypes.byref(n))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_debug_bounds failed")
+    return v.value, i.value, n.value
 
 
 def diagnostics_noalloc(fd, N: int, lam: float = 1.0, phys=None, sums=None, flags=None, stream=None) -> int:

@@ -53,3 +53,17 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _bounds_record(request):
+    """Under the bounds-checked debug build (LBM_BOUNDS_CHECK=1, the library chosen by LBM_LIBRARY), every
+    GPU test must leave the library's record of out-of-range indices empty, and the build must have the
+    checks compiled in."""
+    yield
+    if os.environ.get("LBM_BOUNDS_CHECK") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    from paper_1802_02369_gb300 import lbm
+
+    violations, index, extent = lbm.debug_bounds()
+    assert violations == 0, f"{violations} out-of-range accesses (first index {index}, extent {extent})"
