@@ -44,8 +44,8 @@ WORKLOAD = "steepening acoustic wave, single periodic lattice N=2^26, lambda=1, 
 # expm1 included, from ncu at (1, 256, 2), N = 2^23: (2 DFMA + DADD + DMUL) / nodes.
 # The same FP32 node update in FMA-pipe lane operations (an add, a multiply or a fused multiply-add is
 # one): 19 + 22 + 33 = 74 per node-step, the 3 reciprocals running on the multi-function unit (ncu's
-# paired-instruction counts at (8, 128, 4), N = 2^23: 2 (FADD2 + FFMA2 + FMUL2) / computed node-steps
-# = 74.0; profiles/step_tiles_f32_k8_128x4_N8M.md).
+# paired-instruction counts at (8, 128, 4), N = 2^23, ghost-refresh tiles: 2 (FADD2 + FFMA2 + FMUL2) /
+# computed node-steps = 2 x 2,788,102,144 / (18397 x 512 x 8) = 74.0; profiles/step_tiles_f32_k8_128x4_N8M.md).
 LANE_OPS_PER_NODE_F32 = 74.0
 FLOPS_PER_NODE = {"f32": 110.0, "f64": (2 * 507.31008e6 + 194.468864e6 + 194.468864e6) / 8388608}
 METHOD_FLOPS_PER_NODE = 110.0
@@ -57,8 +57,8 @@ FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
 # FADD2 + 19,972,435,968 FFMA2 + 2,326,538,240 FMUL2) thread-instructions over 17,477 x 512 x 8
 # node-steps = 880.0 (profiles/step_tiles_df_N8M.md).
 DF_FP32_OPS_PER_COMPUTED = 2 * (9198774272 + 19972435968 + 2326538240) / (17477 * 512 * 8)
-TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.51424e6 + 149.390848e6) / 8388608,
-                          ("f64", 1, 256, 2): (403.07968e6 + 347.049472e6) / 8388608}
+TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.524224e6 + 148.761088e6) / 8388608,
+                          ("f64", 1, 256, 2): (403.062016e6 + 347.52768e6) / 8388608}
 
 
 def tile_span_f32(nt: int, v: int) -> int:

@@ -442,8 +442,12 @@ cudaError_t launch_step_tiles(const R* in, R* out, long long plane, const LatDev
 cudaError_t launch_tile_map(const LatDev* lat, int B, long long ntiles, int* map, cudaStream_t st);
 bool valid_tile_config(int K, int NT, int V, bool fp64);
 
-// Work unit of the persistent launch: kUnitTiles consecutive tiles of one time block.
-constexpr int kUnitTiles = 8;
+// Work unit of the persistent launch: kUnitTiles consecutive tiles of one time block (at most 32).
+#ifndef LBM_UNIT_TILES
+#define LBM_UNIT_TILES 16
+#endif
+constexpr int kUnitTiles = LBM_UNIT_TILES;
+static_assert(kUnitTiles >= 1 && kUnitTiles <= 32, "a work unit's tiles are checked by one warp");
 
 // Control block of the persistent launch (device pointers).
 struct PersistentCtl {

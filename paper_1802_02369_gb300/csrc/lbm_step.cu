@@ -130,7 +130,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 template <int NT, int V, bool WALLS, bool FULL>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
-                                                 float (*e_ut)[4], float (*e_f)[4], float2* gbuf) {
+                                                 float (*e_ut)[4], float (*e_f)[4], float2* gbuf, int& gpar) {
   constexpr int NW = NT / 32, NL = V / 2;
   constexpr bool GHOST = V == 4 && NW > 1;
   constexpr int G = kGhost, P = kGhost / 2, WS = 32 * V - 2 * G;  // ghosts per side, refresh period, warp stride
@@ -187,7 +187,11 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   for (int k = 0; k < K; ++k) {
     if constexpr (GHOST) {
       if (k > 0 && k % P == 0) {
-        const int par = (k / P) & 1;
+        // Buffers alternate by a refresh count that runs on across the tiles a CTA processes, so that
+        // the first refresh of a tile never rewrites the buffer the last refresh of the previous tile
+        // is still being read from (the barrier of every refresh separates buffer reuses).
+        const int par = gpar & 1;
+        ++gpar;
         if (lane == 30 && warp < NW - 1) {
 #pragma unroll
           for (int l = 0; l < NL; ++l)
@@ -324,17 +328,17 @@ struct GhostSlots {
 template <typename R, int NT, int V>
 __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                             int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
-                                            R (*e_f)[4], float2* gbuf) {
+                                            R (*e_f)[4], float2* gbuf, int& gpar) {
   // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
   if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
     // The paper's scheme (nonlinear equilibria, entropy source) without per-node mode tests.
     const bool full = c.eq_mode == 0 && c.source_on;
     if (d.bc == 0) {
-      if (full) tile_body_packed<NT, V, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
-      else tile_body_packed<NT, V, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
+      if (full) tile_body_packed<NT, V, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
+      else tile_body_packed<NT, V, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
     } else {
-      if (full) tile_body_packed<NT, V, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
-      else tile_body_packed<NT, V, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf);
+      if (full) tile_body_packed<NT, V, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
+      else tile_body_packed<NT, V, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
     }
   } else {
     if (d.bc == 0) tile_body<R, NT, V, false>(in, out, plane, d, start, K, c, e_ut, e_f);
@@ -382,11 +386,12 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) step_tiles_kerne
   __shared__ R e_f[NT / 32][4];
   __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
   const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
+  int gpar = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
     if (!in_bounds(L, B)) continue;
     const LatDev d = lat[L];
-    tile_update<R, NT, V>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f, gbuf);
+    tile_update<R, NT, V>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f, gbuf, gpar);
   }
 }
 
@@ -453,6 +458,7 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
   const long long nunits = (ntiles + U - 1) / U;
   const long long total = nblocks * nunits;
   const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
+  int gpar = 0;
   if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);
   __syncthreads();
   for (;;) {
@@ -496,9 +502,9 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
           }
           __nanosleep(100);
         }
-        // The acquire loads above, this fence and the CTA barrier below order every thread's later
-        // (ordinary, L1-cached) loads of the tiles after the neighbours' released writes.
-        __threadfence();
+        // The acquire loads above (each one a relaxed load followed by an acquire fence) and the CTA
+        // barrier below order every thread's later (ordinary, L1-cached) loads of the tiles after the
+        // neighbours' released writes.
       }
       if (threadIdx.x == 0) s_go = go;
     }
@@ -512,12 +518,13 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
         const int L = B > 1 ? tile_lat[i] : 0;
         if (!in_bounds(L, B)) continue;
         const LatDev d = lat[L];
-        tile_update<R, NT, V>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, gbuf);
+        tile_update<R, NT, V>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, gbuf, gpar);
       }
     }
     __syncthreads();
     if (threadIdx.x == 0 && !withheld && in_bounds(k, nunits)) {
-      __threadfence();
+      // A release store is a release fence followed by the store: with the CTA barrier above it
+      // publishes every thread's stores of the unit.
       st_release_gpu(ctl.done + k, (int)(b + 1));
     }
   }
