@@ -477,9 +477,11 @@ def run_linear(args, lbm, torch):
     return out
 
 
-# DRAM bytes per node per persistent launch of the ragged batch from ncu, keyed by (k, NT, V) (None until
-# captured for the current kernel).
-BATCH_TRAFFIC_BYTES_PER_NODE = {}
+# DRAM bytes per node and block of k steps of the persistent launch on the ragged batch, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of one persistent launch over 25 blocks of 8 steps, on
+# the batch selection at 1024 lattices, 33.8 M nodes: (20,723.5 + 20,387.7) MB / (33,783,937 x 25)),
+# keyed by (k, NT, V); profiles/persistent_vs_launch_batch256.md.
+BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20723.49056e6 + 20387.729664e6) / (33783937 * 25)}
 # DRAM bytes per differentiated node-step of the backward sweep from ncu (None until captured).
 ADJOINT_TRAFFIC_BYTES_PER_NODE_STEP = {}
 
