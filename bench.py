@@ -40,14 +40,15 @@ WORKLOAD = "steepening acoustic wave, single periodic lattice N=2^26, lambda=1, 
 # Arithmetic per node-update for the ALU roofline (halo recomputation excluded). FP32: the scaled node
 # update as the step kernel implements it (moments, equation of state with the series log1p and
 # expm1, equilibria, relaxation, source, M^-1): 19 add/sub + 22 mul + 33 fma (2 flops) + 3 reciprocals
-# (1 flop) = 110 flops. FP64: the kernel's executed FP64 arithmetic per node-update, CUDA's log1p and
-# expm1 included, from ncu at (1, 256, 2), N = 2^23: (2 DFMA + DADD + DMUL) / nodes.
+# (1 flop) = 110 flops. FP64: the kernel's executed FP64 arithmetic per node-update from ncu at (1, 256, 2),
+# N = 2^23: (2 DFMA + DADD + DMUL) / nodes = 95.8 (its log1p and expm1 run in double-float on the FP32
+# pipes, the reciprocals as FP32 estimates refined by FP64 Newton steps; the FP64 pipe is 85 % busy).
 # The same FP32 node update in FMA-pipe lane operations (an add, a multiply or a fused multiply-add is
 # one): 19 + 22 + 33 = 74 per node-step, the 3 reciprocals running on the multi-function unit (ncu's
 # paired-instruction counts at (8, 128, 4), N = 2^23, ghost-refresh tiles: 2 (FADD2 + FFMA2 + FMUL2) /
 # computed node-steps = 2 x 2,788,102,144 / (18397 x 512 x 8) = 74.0; profiles/step_tiles_f32_k8_128x4_N8M.md).
 LANE_OPS_PER_NODE_F32 = 74.0
-FLOPS_PER_NODE = {"f32": 110.0, "f64": (2 * 507.31008e6 + 194.468864e6 + 194.468864e6) / 8388608}
+FLOPS_PER_NODE = {"f32": 110.0, "f64": (2 * 236744704 + 177558528 + 152193024) / 8388608}
 METHOD_FLOPS_PER_NODE = 110.0
 # Peak arithmetic per SM per clock from the unit counts: 128 FP32 FMA lanes (256 flops); FP64 at
 # 2 FMA per SM per clock (4 flops; the nominal 1.25 TFLOP/s of the part at 152 SMs, 2.07 GHz).
@@ -482,8 +483,22 @@ def run_linear(args, lbm, torch):
 # the batch selection at 1024 lattices, 33.8 M nodes: (20,723.5 + 20,387.7) MB / (33,783,937 x 25)),
 # keyed by (k, NT, V); profiles/persistent_vs_launch_batch256.md.
 BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20723.49056e6 + 20387.729664e6) / (33783937 * 25)}
-# DRAM bytes per differentiated node-step of the backward sweep from ncu (None until captured).
-ADJOINT_TRAFFIC_BYTES_PER_NODE_STEP = {}
+# DRAM bytes of the backward sweep over its algorithmic bytes, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of every recompute and adjoint-block launch between the misfit seed and the
+# initial-state adjoint) on 256 x 65536 nodes (larger than L2), T = 64 (FP32, 4 reverse steps per
+# launch) and T = 16 (FP64, 1; double-float, 4): 23.13 / 24, 211.78 / 216 and 35.49 / 36 B per
+# differentiated node-step. The benchmark reports this ratio times its own algorithmic bytes.
+ADJOINT_TRAFFIC_RATIO = {"f32": 23.13 / 24.0, "f64": 211.78 / 216.0, "f64df": 35.49 / 36.0}
+
+
+def adjoint_bytes_per_node_step(word: int, k: int, T: int) -> float:
+    """Algorithmic bytes per differentiated node-step of the backward sweep: per block of k reverse steps
+    one adjoint-block launch (state and a(t + k) read, a(t) written: 18 words) and, for every block that
+    does not start at a checkpoint, one k-step recompute launch of its starting state (12 words); a
+    segment of S = round(sqrt(T)) steps holds ceil(S / k) blocks, one starting at its checkpoint."""
+    S = max(1, int(round(T ** 0.5)))
+    nb = -(-S // k)
+    return word * (18.0 + 12.0 * (nb - 1) / nb) / k
 
 
 def run_adjoint(args, lbm, torch, hbm_peak: float):
@@ -534,11 +549,8 @@ def run_adjoint(args, lbm, torch, hbm_peak: float):
         lat.close()
         del d, target, rho_T, seed, g_rho, g_u
         torch.cuda.empty_cache()
-        # Backward sweep, per differentiated node-step: the block-start states recomputed from the
-        # checkpoints by k-step launches of the step kernel (one state read and written per k steps) and
-        # one adjoint block launch per k steps (state and a(t + k) read, a(t) written): 30 words / k.
         word = 4 if prec == "f32" else 8
-        bpn = 30 * word / adj_k
+        bpn = adjoint_bytes_per_node_step(word, adj_k, T)
         ach = B * N * T * bpn / bwd_s / 1e9
         out[prec] = {"value": B * N * T / dt / 1e9, "unit": "GLUPS (differentiated node-steps / s)", "T": T,
                      "lattices": B, "N": N, "seconds": dt, "backward_seconds": bwd_s,
@@ -548,7 +560,8 @@ def run_adjoint(args, lbm, torch, hbm_peak: float):
                                                             "launches), CUDA events on the library stream",
                                   "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                                   "algorithmic_bytes_per_node_step": bpn,
-                                  "traffic": ADJOINT_TRAFFIC_BYTES_PER_NODE_STEP.get((prec, adj_k)),
+                                  "traffic": ADJOINT_TRAFFIC_RATIO[prec] * bpn * B * N * T,
+                                  "traffic_unit": "bytes of the whole backward sweep (ncu ratio x algorithmic)",
                                   "note": "arithmetic-bound in practice (ncu: DRAM well below peak)"}}
     return out
 

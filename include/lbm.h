@@ -193,8 +193,9 @@ int lbm_debug_eval_f32(const float *x, float *y, int64_t n, int32_t fn, void *st
 
 /* Test hook: the double-float operations of the LBM_F64_DF step, elementwise on n doubles (device
  * pointers, enqueued on stream), each input split into hi + lo floats and the result summed back to
- * FP64: fn 0 = log(1+x), 1 = exp(x)-1, 2 = 1/x, 3 = x*x2, 4 = x+x2, 5 = x*x2[i] + x2[(i+1) mod n]
- * (x2 unused and may be NULL for fn 0-2). */
+ * FP64: fn 0 = log(1+x), 1 = exp(x)-1, 2 = 1/x, 3 = x*x2, 4 = x+x2, 5 = x*x2[i] + x2[(i+1) mod n];
+ * fn 6, 7, 8 = the FP64-lane log(1+x), exp(x)-1 and 1/x of the LBM_F64 node update (double-float series
+ * and FP64 Newton steps), on the FP64 input (x2 unused and may be NULL for fn 0-2 and 6-8). */
 int lbm_debug_eval_df(const double *x, const double *x2, double *y, int64_t n, int32_t fn, void *stream);
 
 /* Times every valid (k, block_threads, nodes_per_thread) on the current state (which is left

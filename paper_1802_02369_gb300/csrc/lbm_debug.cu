@@ -31,8 +31,9 @@ extern "C" int lbm_debug_eval_f32(const float* x, float* y, int64_t n, int32_t f
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-// Test hook for the double-float functions of lbm_df.cuh: y = f(x) elementwise, computed in
-// double-float from the FP64 input (split into hi + lo) and summed back to FP64.
+// Test hook for the double-float functions of lbm_df_core.cuh: y = f(x) elementwise, computed in
+// double-float from the FP64 input (split into hi + lo) and summed back to FP64 (fn 0-5); fn 6-8 the
+// FP64-lane log1p, expm1 and reciprocal of the node update.
 namespace {
 
 __global__ void eval_df_kernel(const double* __restrict__ x, const double* __restrict__ x2, double* __restrict__ y,
@@ -47,7 +48,11 @@ __global__ void eval_df_kernel(const double* __restrict__ x, const double* __res
     case 2: r = lbm::m_rcp(a); break;
     case 3: r = lbm::ml(a, lbm::to_df(x2[i])); break;
     case 4: r = lbm::ad(a, lbm::to_df(x2[i])); break;
-    default: r = lbm::fm(a, lbm::to_df(x2[i]), lbm::to_df(x2[(i + 1) % n])); break;
+    case 5: r = lbm::fm(a, lbm::to_df(x2[i]), lbm::to_df(x2[(i + 1) % n])); break;
+    // The FP64 lanes of the node update, on the FP64 input itself.
+    case 6: y[i] = lbm::m_log1p(x[i]); return;
+    case 7: y[i] = lbm::m_expm1(x[i]); return;
+    default: y[i] = lbm::m_rcp(x[i]); return;
   }
   y[i] = lbm::to_double(r);
 }
@@ -55,7 +60,7 @@ __global__ void eval_df_kernel(const double* __restrict__ x, const double* __res
 }  // namespace
 
 extern "C" int lbm_debug_eval_df(const double* x, const double* x2, double* y, int64_t n, int32_t fn, void* stream) {
-  if (!x || !y || n < 1 || fn < 0 || fn > 5 || (fn >= 3 && !x2)) return LBM_ERR_INVALID_ARG;
+  if (!x || !y || n < 1 || fn < 0 || fn > 8 || (fn >= 3 && fn <= 5 && !x2)) return LBM_ERR_INVALID_ARG;
   eval_df_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, x2, y, n, fn);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm_df_core.cuh"
+
 namespace lbm {
 
 // Bounds-checked debug build. Compiled with -DLBM_DEBUG_BOUNDS, the step, persistent, double-float and
@@ -119,16 +121,17 @@ __device__ __forceinline__ float2 ml(float2 a, float2 b) { return __fmul2_rn(a, 
 __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float2 fm(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// Reciprocals: FP32 uses the hardware approximation, one MUFU operation (relative error about 2^-23;
-// subnormal inputs and results flush to zero, which the positive, order-one denominators of the node
-// update never reach), FP64 the correctly rounded reciprocal.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
+// Reciprocals: FP32 uses the hardware approximation (rcp_approx, lbm_df_core.cuh), one MUFU operation.
+// FP64 refines the same FP32 estimate by two Newton-Raphson steps in FP64, y <- y + y (1 - x y), each
+// squaring the relative error (about 2^-23, then 2^-46, then below FP64 rounding): four FP64 fused
+// multiply-adds, where this GPU's FP64 pipe runs 2 per SM and clock. The node update's denominators
+// are positive and of order one, far inside FP32 range.
 __device__ __forceinline__ float m_rcp(float x) { return rcp_approx(x); }
-__device__ __forceinline__ double m_rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ double m_rcp(double x) {
+  double y = (double)rcp_approx((float)x);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
 __device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(rcp_approx(x.x), rcp_approx(x.y)); }
 
 // log(1 + x) and exp(x) - 1. double and float use CUDA's functions. On paired lanes they are
@@ -139,9 +142,13 @@ __device__ __forceinline__ float2 m_rcp(float2 x) { return make_float2(rcp_appro
 //  - expm1(x) = 2^k expm1(r) + (2^k - 1), x = k ln 2 + r, |r| <= ln(2)/2 (k = 0 for |x| <= 0.35),
 //    expm1(r) = r + r^2 (1/2! + r/3! + ... + r^5/7!) (first omitted term r^8/8! below 2e-8 of
 //    expm1(r), a third of an FP32 ulp).
-__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+// FP64 lanes evaluate log1p and expm1 in double-float on the FP32 pipes (the series of
+// lbm_df_core.cuh for |x| <= 0.3 and |x| <= 0.35, relative error below 2^-45, CUDA's FP64 functions
+// outside), the argument split into hi + lo and the result summed back: GB300's FP32 pipes are 64 times
+// wider than its FP64 pipe, where these two functions took a third of the node update's FP64 work.
+__device__ __forceinline__ double m_log1p(double x) { return to_double(m_log1p(to_df(x))); }
 __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ double m_expm1(double x) { return to_double(m_expm1(to_df(x))); }
 __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
 
 __device__ __forceinline__ float2 atanh2_series(float2 t) {  // 2 atanh(t / (2 + t)) for |t| <= 0.5

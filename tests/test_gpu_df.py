@@ -69,6 +69,27 @@ def test_series_accuracy(lbm, fn, ref, lim):
     assert (np.abs(got - exact) / np.abs(exact)).max() <= 2.0 ** -46
 
 
+def test_fp64_lane_functions(lbm):
+    """The FP64 lanes of the LBM_F64 node update: log1p and expm1 evaluated in double-float from the FP64
+    argument (its split into hi + lo loses under 2^-48 of it) against numpy's FP64 functions of the
+    argument itself, and the reciprocal (an FP32 estimate and two FP64 Newton steps) against 1/x, over
+    the node update's ranges (densities and temperatures of order one) and across the series limits."""
+    rng = np.random.default_rng(9)
+    for fn, ref, lim in ((6, np.log1p, 0.3), (7, np.expm1, 0.35)):
+        x = np.concatenate([np.linspace(-lim, lim, 100001), rng.uniform(-lim, lim, 100000),
+                            rng.uniform(0.3, 3.0, 20000) * rng.choice([-1.0, 1.0], 20000),
+                            [0.0, 1e-30, -1e-20, 1e-9, lim, -lim]])
+        if fn == 6:
+            x = x[x > -0.9]
+        got = _eval(lbm, fn, x)
+        exact = ref(x)
+        rel = np.abs(got - exact) / np.maximum(np.abs(exact), 1e-300)
+        assert rel.max() <= 2.0 ** -44, (fn, rel.max())
+    x = np.concatenate([np.linspace(0.05, 5.0, 200001), 10.0 ** rng.uniform(-3, 3, 100000), [1.0, 2.0, 0.75]])
+    got = _eval(lbm, 8, x)
+    assert (np.abs(got - 1.0 / x) / (1.0 / x)).max() <= 2.0 ** -51
+
+
 def test_basic_operations_accuracy(lbm):
     rng = np.random.default_rng(6)
     n = 200000
