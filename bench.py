@@ -572,13 +572,13 @@ def run_adjoint(args, lbm, torch, hbm_peak: float):
 FD_NU = 1.0 / S_E - 0.5
 FD_DT = 1.0
 FD_BYTES_PER_NODE = {"f32": 24, "f64": 48}
-# Arithmetic per computed node-step of the finite-difference kernel (halo included). FP64: executed, from
-# ncu at N = 2^23, (4, 256, 1): (2 x 1,766,529,024 DFMA + 831,307,776 DADD + 831,307,776 DMUL) over
-# 33,826 x 256 x 4 node-steps = 150.0 (CUDA's log1p, expm1 and reciprocals included). FP32 runs two nodes
+# Arithmetic per computed node-step of the finite-difference kernel (halo included). FP64: executed on the
+# FP64 pipe, from ncu at N = 2^23, (4, 256, 1): (2 DFMA + DADD + DMUL) = 2,736,388,096 over 33,826 x 256 x 4
+# node-steps = 79.0 (log1p and expm1 run in double-float on the FP32 pipes). FP32 runs two nodes
 # per paired lane, which ncu's per-opcode counters do not split out; counted from the source (fma = 2):
 # 57 for the nodal quantities (series log1p 20 and expm1 13 included) + 37 for the update = 94. Per
 # output node-update this is multiplied by the tile's computed / stored nodes, NT V / (NT V - 2K).
-FD_FLOPS_PER_COMPUTED = {"f64": 5195673600 / 34637824, "f32": 94.0}
+FD_FLOPS_PER_COMPUTED = {"f64": 2736388096 / 34637824, "f32": 94.0}
 
 
 def run_fd(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
@@ -630,14 +630,14 @@ def run_fd(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
 # the advection-diffusion scheme on zeta = 1 + 0.1 sin (u0 = 0.1, alpha = 0, s_psi = 1.2, s_eps = 1.5).
 # Bytes per node per launch: three populations read and written.
 D1Q3_BYTES_PER_NODE = {"f32": 24, "f64": 48}
-# Arithmetic per computed node-step (halo included), keyed by (scheme, precision). FP64: executed
-# DFMA, DADD, DMUL from ncu at N = 2^23, (16, 256, 4), over 8457 x 1024 x 16 node-steps (CUDA's log1p,
-# expm1 and reciprocal included): fluid (2 x 5,819,498,496 + 1,662,713,856 + 1,524,154,368) / 138,559,488
-# = 107.0, advection-diffusion (2 x 831,356,928 + 831,356,928 + 554,237,952) / 138,559,488 = 22.0.
+# Arithmetic per computed node-step (halo included), keyed by (scheme, precision). FP64: executed on the
+# FP64 pipe (2 DFMA + DADD + DMUL) from ncu at N = 2^23, (16, 256, 4), over 8457 x 1024 x 16 node-steps:
+# fluid 5,265,260,544 / 138,559,488 = 38.0 (its log1p and expm1 in double-float on the FP32 pipes),
+# advection-diffusion 3,048,308,736 / 138,559,488 = 22.0.
 # FP32 runs on paired lanes, which ncu's per-opcode counters do not split out; counted from the source
 # instead (fma = 2): fluid 60 (moments 5, 1/(1+r) 2, series log1p 20 and expm1 13, equilibrium and
 # relaxation 11, M^-1 9), advection-diffusion 22 (the FP64 count).
-D1Q3_FLOPS_PER_COMPUTED = {("fluid", "f64"): 14825865216 / 138559488, ("advection_diffusion", "f64"): 22.0,
+D1Q3_FLOPS_PER_COMPUTED = {("fluid", "f64"): 5265260544 / 138559488, ("advection_diffusion", "f64"): 22.0,
                            ("fluid", "f32"): 60.0, ("advection_diffusion", "f32"): 22.0}
 
 

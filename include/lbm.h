@@ -157,7 +157,7 @@ int lbm_get_config(const lbm_ctx *ctx, int32_t *steps_per_launch, int32_t *block
 /* Execution mode of lbm_step.
  * LBM_MODE_LAUNCH: one kernel launch per k steps (default).
  * LBM_MODE_PERSISTENT: all whole blocks of k steps in ONE persistent launch; CTAs claim work units
- *   (a block of k steps on 8 consecutive tiles) in order, and a unit waits only for the units holding
+ *   (a block of k steps on 16 consecutive tiles) in order, and a unit waits only for the units holding
  *   its tiles' lattice neighbours to finish the previous block (bounded spin; see lbm_status).
  *   Results are bitwise equal to LBM_MODE_LAUNCH.
  * LBM_MODE_PERSISTENT_GRAPH: the same launch (with its counter resets) captured once in a CUDA graph
@@ -172,7 +172,7 @@ int lbm_set_mode(lbm_ctx *ctx, int32_t mode);
 int lbm_status(lbm_ctx *ctx);
 
 /* Failure-detection test hook for persistent launches: spin_limit >= 1 polls (about 100 ns apart)
- * before a wait gives up (default 2e7), and withhold_tile >= 0 names a work unit (8 consecutive tiles)
+ * before a wait gives up (default 2e7), and withhold_tile >= 0 names a work unit (16 consecutive tiles)
  * whose first time block is never computed nor released, so that its neighbours' waits must expire
  * (-1: none). */
 int lbm_debug_persistent(lbm_ctx *ctx, int64_t spin_limit, int64_t withhold_tile);

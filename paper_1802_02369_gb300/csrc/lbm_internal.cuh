@@ -369,6 +369,13 @@ __device__ __forceinline__ bool node_state_s(const X f[6], const Consts<X>& c, X
   return ok;
 }
 
+// The entropy source z + dt S in scaled moments, dt S = q_src (1 + r)/theta [du'^2 + dtheta^2 / (Pr theta)]
+// with the centred differences du' = u'_{j+1} - u'_{j-1}, dtheta likewise, is written out in the node
+// update below for the FP32 and FP64 lanes; the double-float lanes (lbm_df.cuh) give their own
+// source_update, found where the node update is instantiated.
+template <typename X>
+constexpr bool kSourceOverloaded = false;
+
 template <typename X, bool FULL = false>
 __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X thl, X thr, X s_e, X s_psi,
                                                X s_eps, X q_src, X s0h, const Consts<X>& c, X fs[6],
@@ -393,10 +400,14 @@ __device__ __forceinline__ void node_collide_s(const NodeS<X>& m, X ul, X ur, X 
   // (vii) entropy production (eq. NS-rho-J-zeta), centred differences.
   X zs = m.z;
   if (FULL || c.source_on) {
-    const X du = sb(ur, ul), dth = sb(thr, thl);
-    const X ith = m_rcp(m.th);
-    const X A = fm(ml(dth, dth), ml(ith, c.inv_Pr), ml(du, du));
-    zs = fm(ml(ml(q_src, m.rho1), ith), A, m.z);
+    if constexpr (kSourceOverloaded<X>) {
+      zs = source_update(m.z, m.rho1, m.th, ul, ur, thl, thr, q_src, c.inv_Pr);
+    } else {
+      const X du = sb(ur, ul), dth = sb(thr, thl);
+      const X ith = m_rcp(m.th);
+      const X A = fm(ml(dth, dth), ml(ith, c.inv_Pr), ml(du, du));
+      zs = fm(ml(ml(q_src, m.rho1), ith), A, m.z);
+    }
   }
   // (vi) back to populations.
   {
