@@ -1049,7 +1049,7 @@ int lbm_autotune(lbm_ctx* c, int32_t trials) {
   const int Vs[3] = {1, 2, 4};
   double best = 1e300;
   int bestK = c->K, bestNT = c->NT, bestV = c->V;
-  const long long kTrialTiles = 16384;  // enough waves to be representative; the rest is skipped
+  const long long kTrialTiles = 65536;  // 30 M nodes at 128 x 4: about 50 waves, the rest is skipped
   for (int nt : NTs)
     for (int v : Vs)
       for (int k : Ks) {

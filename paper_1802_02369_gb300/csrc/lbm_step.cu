@@ -130,7 +130,7 @@ __device__ __forceinline__ void tile_body(const R* in, R* out, long long plane, 
 template <int NT, int V, bool WALLS, bool FULL>
 __device__ __forceinline__ void tile_body_packed(const float* in, float* out, long long plane, const LatDev& d,
                                                  long long start, int K, const Consts<float2>& c,
-                                                 float (*e_ut)[4], float (*e_f)[4], float2* gbuf, int& gpar) {
+                                                 float (*e_ut)[4], float (*e_f)[4], float2* gbuf, int tpar) {
   constexpr int NW = NT / 32, NL = V / 2;
   constexpr bool GHOST = V == 4 && NW > 1;
   constexpr int G = kGhost, P = kGhost / 2, WS = 32 * V - 2 * G;  // ghosts per side, refresh period, warp stride
@@ -187,11 +187,13 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
   for (int k = 0; k < K; ++k) {
     if constexpr (GHOST) {
       if (k > 0 && k % P == 0) {
-        // Buffers alternate by a refresh count that runs on across the tiles a CTA processes, so that
-        // the first refresh of a tile never rewrites the buffer the last refresh of the previous tile
-        // is still being read from (the barrier of every refresh separates buffer reuses).
-        const int par = gpar & 1;
-        ++gpar;
+        // Buffers alternate by refresh (the barrier of every refresh separates two uses of a buffer).
+        // A tile of K = 8 or 4 steps has an odd number of refreshes (3 or 1), so offsetting the parity
+        // by tpar, the parity of the tile's place among tiles a CTA runs back to back without a CTA
+        // barrier between them (the persistent kernel's work units), keeps the alternation across
+        // tiles: the first refresh of a tile never rewrites the buffer the previous tile's last refresh
+        // is still being read from.
+        const int par = ((k / P) + tpar) & 1;
         if (lane == 30 && warp < NW - 1) {
 #pragma unroll
           for (int l = 0; l < NL; ++l)
@@ -328,17 +330,17 @@ struct GhostSlots {
 template <typename R, int NT, int V>
 __device__ __forceinline__ void tile_update(const R* in, R* out, long long plane, const LatDev& d, long long start,
                                             int K, const Consts<typename Lanes<R, V>::type>& c, R (*e_ut)[4],
-                                            R (*e_f)[4], float2* gbuf, int& gpar) {
+                                            R (*e_f)[4], float2* gbuf, int tpar) {
   // Periodic tiles take the wall-free path; bounce-back lattices the one with wall handling.
   if constexpr (std::is_same<typename Lanes<R, V>::type, float2>::value) {
     // The paper's scheme (nonlinear equilibria, entropy source) without per-node mode tests.
     const bool full = c.eq_mode == 0 && c.source_on;
     if (d.bc == 0) {
-      if (full) tile_body_packed<NT, V, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
-      else tile_body_packed<NT, V, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
+      if (full) tile_body_packed<NT, V, false, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, tpar);
+      else tile_body_packed<NT, V, false, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, tpar);
     } else {
-      if (full) tile_body_packed<NT, V, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
-      else tile_body_packed<NT, V, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, gpar);
+      if (full) tile_body_packed<NT, V, true, true>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, tpar);
+      else tile_body_packed<NT, V, true, false>(in, out, plane, d, start, K, c, e_ut, e_f, gbuf, tpar);
     }
   } else {
     if (d.bc == 0) tile_body<R, NT, V, false>(in, out, plane, d, start, K, c, e_ut, e_f);
@@ -386,12 +388,15 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) step_tiles_kerne
   __shared__ R e_f[NT / 32][4];
   __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
   const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
-  int gpar = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
-    if (!in_bounds(L, B)) continue;
-    const LatDev d = lat[L];
-    tile_update<R, NT, V>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f, gbuf, gpar);
+    if (in_bounds(L, B)) {
+      const LatDev d = lat[L];
+      tile_update<R, NT, V>(in, out, plane, d, (tile - d.tile0) * bout, K, c, e_ut, e_f, gbuf, 0);
+    }
+    // A CTA that has another tile (a grid smaller than the tile count) waits for all its warps first:
+    // the shared edge and ghost buffers are reused.
+    if (tile + gridDim.x < ntiles) __syncthreads();
   }
 }
 
@@ -458,7 +463,6 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
   const long long nunits = (ntiles + U - 1) / U;
   const long long total = nblocks * nunits;
   const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
-  int gpar = 0;
   if (threadIdx.x == 0) s_next = (long long)atomicAdd(ctl.counter, 1ULL);
   __syncthreads();
   for (;;) {
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
         const int L = B > 1 ? tile_lat[i] : 0;
         if (!in_bounds(L, B)) continue;
         const LatDev d = lat[L];
-        tile_update<R, NT, V>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, gbuf, gpar);
+        tile_update<R, NT, V>(in, out, plane, d, (i - d.tile0) * bout, K, c, e_ut, e_f, gbuf, (int)(i & 1));
       }
     }
     __syncthreads();
