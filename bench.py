@@ -59,6 +59,7 @@ FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
 # node-steps = 880.0 (profiles/step_tiles_df_N8M.md).
 DF_FP32_OPS_PER_COMPUTED = 2 * (9198774272 + 19972435968 + 2326538240) / (17477 * 512 * 8)
 TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.524224e6 + 148.761088e6) / 8388608,
+                          ("f32", 8, 64, 4): (201.4528e6 + 148.866816e6) / 8388608,
                           ("f64", 1, 256, 2): (403.062016e6 + 347.52768e6) / 8388608}
 
 
