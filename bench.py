@@ -54,12 +54,13 @@ METHOD_FLOPS_PER_NODE = 110.0
 # 2 FMA per SM per clock (4 flops; the nominal 1.25 TFLOP/s of the part at 152 SMs, 2.07 GHz).
 FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
 # FP32 operations (each lane of FADD2 / FFMA2 / FMUL2 one lane-operation) per computed node-step of
-# the double-float step kernel on paired lanes, from ncu at N = 2^23, (8, 128, 4): 2 x (9,198,774,272
-# FADD2 + 19,972,435,968 FFMA2 + 2,326,538,240 FMUL2) thread-instructions over 17,477 x 512 x 8
-# node-steps = 880.0 (profiles/step_tiles_df_N8M.md).
-DF_FP32_OPS_PER_COMPUTED = 2 * (9198774272 + 19972435968 + 2326538240) / (17477 * 512 * 8)
-TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.524224e6 + 148.761088e6) / 8388608,
-                          ("f32", 8, 64, 4): (201.4528e6 + 148.866816e6) / 8388608,
+# the double-float step kernel on paired lanes, from ncu at N = 2^23, (8, 128, 4), entropy source in
+# FP32 where it is below 2^-32 of the field scale: 2 x (8,805,052,416 FADD2 + 18,397,548,544 FFMA2 +
+# 2,183,366,656 FMUL2) thread-instructions (no scalar FADD / FFMA / FMUL) over 17,477 x 512 x 8
+# node-steps = 821.0 (profiles/step_tiles_df_N8M.md).
+DF_FP32_OPS_PER_COMPUTED = 2 * (8805052416 + 18397548544 + 2183366656) / (17477 * 512 * 8)
+TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.41696e6 + 153.121792e6) / 8388608,
+                          ("f32", 8, 64, 4): (201.407744e6 + 153.624832e6) / 8388608,
                           ("f64", 1, 256, 2): (403.062016e6 + 347.52768e6) / 8388608}
 
 
@@ -483,7 +484,7 @@ def run_linear(args, lbm, torch):
 # (dram__bytes_read.sum + dram__bytes_write.sum of one persistent launch over 25 blocks of 8 steps, on
 # the batch selection at 1024 lattices, 33.8 M nodes: (20,723.5 + 20,387.7) MB / (33,783,937 x 25)),
 # keyed by (k, NT, V); profiles/persistent_vs_launch_batch256.md.
-BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20723.49056e6 + 20387.729664e6) / (33783937 * 25)}
+BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20736.672768e6 + 20420.08576e6) / (33783937 * 25)}
 # DRAM bytes of the backward sweep over its algorithmic bytes, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of every recompute and adjoint-block launch between the misfit seed and the
 # initial-state adjoint) on 256 x 65536 nodes (larger than L2), T = 64 (FP32, 4 reverse steps per

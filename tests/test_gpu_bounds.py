@@ -1,9 +1,10 @@
 """The bounds-checked debug build: the library compiled with -DLBM_DEBUG_BOUNDS checks every global and
 shared-memory index of the step, persistent, double-float and adjoint kernels before the access, and
 counts instead of faulting. The edge-size parity tests (lattices of 3 to 4099 nodes on every tile shape
-and depth, ragged periodic and bounce-back batches, paired FP32 lanes at walls and joints, the persistent
-and graph modes with their bounded waits, the linear variant, the double-float kernels, the adjoint at
-every depth) run again in a child process on that build, and every one must leave the record empty."""
+and depth, ragged periodic and bounce-back batches, paired FP32 lanes at walls and joints, the vector
+and per-node memory paths, the persistent and graph modes with their bounded waits, the linear variant,
+the double-float kernels, the adjoint at every depth) run again in a child process on that build, and
+every one must leave the record empty."""
 import os
 import subprocess
 import sys
@@ -16,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 SELECTION = [
     ("tests/test_gpu_parity.py", "small_and_ragged or paired_lane or batched_ragged or persistent_and_graph "
-                                 "or wait_timeout or linear_variant or sod_fp64"),
+                                 "or wait_timeout or linear_variant or sod_fp64 or vector_and_per_node"),
     ("tests/test_gpu_df.py", "configurations_agree or paired_lanes or ragged_bounce or sod_against or modes_and"),
     ("tests/test_gpu_adjoint.py", "dual_numbers or depths_agree or double_float or fp32_close"),
     ("tests/test_gpu_phys.py", "per_lattice"),

@@ -189,6 +189,49 @@ def test_fp32_paired_lane_layouts_agree(O, lbm):
         assert rel_err(tuple(m[lo:hi].T), ref, scales()).max() <= 1e-5, b
 
 
+def test_vector_and_per_node_memory_paths_agree(O, lbm):
+    """FP32 threads whose nodes are V-aligned and inside their lattice move populations as float4 /
+    float2 vectors, the others node by node. Lattice lengths 1 to 4 mod 4 put the batch's lattice
+    offsets at every residue mod 4 (vector path only in the aligned ones), depth 1 has a 2-node halo
+    (per-node path everywhere), and a lattice run alone starts at offset 0 (vector path): every run
+    must give bitwise the same populations, and the batch stays within the FP32 tolerance of the
+    oracle."""
+    ph = O.default_phys()
+    lengths = np.array([1001, 1002, 1003, 1004, 2049, 3, 514, 1027])
+    bcs = np.array([0, 1, 0, 1, 1, 0, 0, 1])
+    s_e = np.array([1.0, 1.2, 1.5, 1.9, 1.1, 1.3, 1.2, 1.6])
+    offs = np.concatenate([[0], np.cumsum(lengths)])
+    rho, u, p = [], [], []
+    for b, n in enumerate(lengths):
+        r, v, q = smooth_data(int(n), 600 + b, bc=int(bcs[b]), p_ref=ph.p0)
+        rho.append(r); u.append(v); p.append(q)
+    rho, u, p = (np.concatenate(x) for x in (rho, u, p))
+    nsteps = 24
+    runs = []
+    for cfg in ((8, 128, 4), (8, 64, 4), (4, 128, 2), (1, 128, 4)):
+        lat = lbm.Lattice(lengths, s_e=s_e, bc=bcs, precision="f32")
+        lat.set_config(*cfg)
+        lat.set_state(rho, u, p)
+        lat.step(nsteps)
+        runs.append(lat.populations())
+        m = np.stack(lat.moments(device=False), axis=1)
+        lat.close()
+    for pop in runs[1:]:
+        assert np.array_equal(pop, runs[0])
+    for b, n in enumerate(lengths):
+        lo, hi = offs[b], offs[b + 1]
+        lat = lbm.Lattice(int(n), s_e=float(s_e[b]), bc=int(bcs[b]), precision="f32")
+        lat.set_config(8, 128, 4)
+        lat.set_state(rho[lo:hi], u[lo:hi], p[lo:hi])
+        lat.step(nsteps)
+        alone = lat.populations()
+        lat.close()
+        assert np.array_equal(alone, runs[0][:, lo:hi]), b
+        phb = O.default_phys(bc=int(bcs[b]))
+        ref = O.moments(phb, O.run(phb, O.coupled_rates(s_e[b]), O.init(phb, rho[lo:hi], u[lo:hi], p=p[lo:hi]), nsteps))
+        assert rel_err(tuple(m[lo:hi].T), ref, scales()).max() <= 1e-5, b
+
+
 def test_batched_ragged_fp64(O, lbm):
     """Independent lattices of uneven lengths, rates and boundaries in one context."""
     rng = np.random.default_rng(1802)
