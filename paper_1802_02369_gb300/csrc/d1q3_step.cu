@@ -22,6 +22,7 @@
 // step; the edge buffers alternate by step parity).
 #include "d1q3_internal.cuh"
 #include "lbm_internal.cuh"
+#include "vec_io.cuh"
 
 namespace lbm {
 
@@ -97,12 +98,22 @@ __global__ void __launch_bounds__(NT) d1q3_step_kernel(const R* __restrict__ in,
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long pos0 = tile * bout - K + (long long)threadIdx.x * V;
     X f[NL][3];
+    if (VecIo<R, V>::ok(in, pos0, N)) {  // lanes hold consecutive nodes: vectors map onto them
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      long long lp = pos0 + v;
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+      for (int i = 0; i < 3; ++i) {
+        R t[V];
+        VecIo<R, V>::load(in + i * N + pos0, t);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) lset(f[v / W][i], v % W, in[i * N + lp]);
+        for (int v = 0; v < V; ++v) lset(f[v / W][i], v % W, t[v]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        long long lp = pos0 + v;
+        if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) lset(f[v / W][i], v % W, in[i * N + lp]);
+      }
     }
     for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -133,13 +144,24 @@ __global__ void __launch_bounds__(NT) d1q3_step_kernel(const R* __restrict__ in,
         carry = t;
       }
     }
+    const int local0 = threadIdx.x * V;
+    if (local0 >= K && local0 + V <= K + bout && VecIo<R, V>::ok(out, pos0, N)) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int local = threadIdx.x * V + v;
-      const long long pos = pos0 + v;
-      if (local >= K && local < K + bout && pos < N)
+      for (int i = 0; i < 3; ++i) {
+        R t[V];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) out[i * N + pos] = lget(f[v / W][i], v % W);
+        for (int v = 0; v < V; ++v) t[v] = lget(f[v / W][i], v % W);
+        VecIo<R, V>::store(out + i * N + pos0, t);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int local = local0 + v;
+        const long long pos = pos0 + v;
+        if (local >= K && local < K + bout && pos < N)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) out[i * N + pos] = lget(f[v / W][i], v % W);
+      }
     }
     __syncthreads();  // the next tile's first step rewrites the edge buffer
   }

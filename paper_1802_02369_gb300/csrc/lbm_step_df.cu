@@ -136,16 +136,38 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
     const long long pos = pos0 + v;
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
-    long long lp = pos;
-    if (!WALLS) {
-      if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
-    } else {
-      lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
-    }
-    const double* src = in + off + lp;
-    const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
+  }
+  // A lane pair holds two consecutive nodes, so where the thread's V nodes lie inside the lattice at
+  // an even place of even planes (a 16-byte-aligned buffer) each pair moves as one double2, loaded
+  // and stored; lattice ends, odd offsets of a batch and odd halos take the per-node path.
+  const auto vec_at = [&](const double* base) {
+    return (((off + pos0) | plane) & 1) == 0 && pos0 >= 0 && pos0 + V <= N &&
+           (reinterpret_cast<unsigned long long>(base) & 15) == 0 && in_bounds(pos0 + V - 1, N) &&
+           in_bounds(off + pos0 + V - 1, plane);
+  };
+  if (vec_at(in)) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) df2_set(f[v >> 1][i], v & 1, to_df(ok ? src[i * plane] : 0.0));
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double2 x = *reinterpret_cast<const double2*>(in + off + pos0 + 2 * l + i * plane);
+        df2_set(f[l][i], 0, to_df(x.x));
+        df2_set(f[l][i], 1, to_df(x.y));
+      }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      long long lp = pos0 + v;
+      if (!WALLS) {
+        if (lp < 0 || lp >= N) { lp %= N; if (lp < 0) lp += N; }
+      } else {
+        lp = lp < 0 ? 0 : (lp >= N ? N - 1 : lp);
+      }
+      const double* src = in + off + lp;
+      const bool ok = in_bounds(lp, N) && in_bounds(off + lp, plane);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) df2_set(f[v >> 1][i], v & 1, to_df(ok ? src[i * plane] : 0.0));
+    }
   }
 
   for (int k = 0; k < K; ++k) {
@@ -198,9 +220,19 @@ __device__ __forceinline__ void tile_body_df2(const double* __restrict__ in, dou
     }
   }
 
+  const int local0 = threadIdx.x * V;
+  if (local0 >= halo && local0 + V <= halo + bout && vec_at(out)) {
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        *reinterpret_cast<double2*>(out + off + pos0 + 2 * l + i * plane) =
+            make_double2(to_double(df2_get(f[l][i], 0)), to_double(df2_get(f[l][i], 1)));
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int local = threadIdx.x * V + v;
+    const int local = local0 + v;
     const long long pos = pos0 + v;
     if (local >= halo && local < halo + bout && pos < N && in_bounds(pos, N) && in_bounds(off + pos, plane)) {
       double* dst = out + off + pos;
