@@ -160,7 +160,17 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
     lw[v] = WALLS && pos == 0;
     rw[v] = WALLS && pos == N - 1;
   }
-  {
+  // A thread whose nodes lie inside the lattice loads them without the per-node wrap or wall clamp.
+  if (pos0 >= 0 && pos0 + V <= N && in_bounds(off + pos0 + V - 1, plane)) {
+    const float* src = in + off + pos0;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const float x = src[v + i * plane];
+        if (v >= NL) f[v - NL][i].y = x; else f[v][i].x = x;
+      }
+  } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       long long lp = pos0 + v;
@@ -194,34 +204,32 @@ __device__ __forceinline__ void tile_body_packed(const float* in, float* out, lo
         // tiles: the first refresh of a tile never rewrites the buffer the previous tile's last refresh
         // is still being read from.
         const int par = ((k / P) + tpar) & 1;
-        if (lane == 30 && warp < NW - 1) {
+        // Lanes 30 (for warp + 1) and 1 (for warp - 1) publish in one pass and lanes 0 and 31 take in
+        // one pass, the twelve float2 of a thread as six 16-byte words (a thread's slots start at a
+        // multiple of 12 float2 of the 16-byte-aligned buffer).
+        if ((lane == 30 && warp < NW - 1) || (lane == 1 && warp > 0)) {
+          const int base = gslot(lane == 1 ? 1 : 0, par, warp, 0, 0);
 #pragma unroll
           for (int l = 0; l < NL; ++l)
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-              if (in_bounds(gslot(0, par, warp, l, i), GS)) gbuf[gslot(0, par, warp, l, i)] = f[l][i];
-        }
-        if (lane == 1 && warp > 0) {
-#pragma unroll
-          for (int l = 0; l < NL; ++l)
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-              if (in_bounds(gslot(1, par, warp, l, i), GS)) gbuf[gslot(1, par, warp, l, i)] = f[l][i];
+            for (int i = 0; i < 6; i += 2)
+              if (in_bounds(base + l * 6 + i + 1, GS))
+                reinterpret_cast<float4*>(gbuf + base + l * 6 + i)[0] =
+                    make_float4(f[l][i].x, f[l][i].y, f[l][i + 1].x, f[l][i + 1].y);
         }
         __syncthreads();
-        if (lane == 0 && warp > 0 && in_bounds(warp - 1, NW)) {
+        if ((lane == 0 && warp > 0) || (lane == 31 && warp < NW - 1)) {
+          const int src = lane == 0 ? warp - 1 : warp + 1;
+          const int base = gslot(lane == 0 ? 0 : 1, par, src, 0, 0);
 #pragma unroll
           for (int l = 0; l < NL; ++l)
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-              if (in_bounds(gslot(0, par, warp - 1, l, i), GS)) f[l][i] = gbuf[gslot(0, par, warp - 1, l, i)];
-        }
-        if (lane == 31 && warp < NW - 1 && in_bounds(warp + 1, NW)) {
-#pragma unroll
-          for (int l = 0; l < NL; ++l)
-#pragma unroll
-            for (int i = 0; i < 6; ++i)
-              if (in_bounds(gslot(1, par, warp + 1, l, i), GS)) f[l][i] = gbuf[gslot(1, par, warp + 1, l, i)];
+            for (int i = 0; i < 6; i += 2)
+              if (in_bounds(src, NW) && in_bounds(base + l * 6 + i + 1, GS)) {
+                const float4 x = reinterpret_cast<const float4*>(gbuf + base + l * 6 + i)[0];
+                f[l][i] = make_float2(x.x, x.y);
+                f[l][i + 1] = make_float2(x.z, x.w);
+              }
         }
       }
     }
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) step_tiles_kerne
                                                         int K, Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
-  __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
+  __shared__ __align__(16) float2 gbuf[GhostSlots<R, NT, V>::value];
   const long long bout = tile_span(NT, V, sizeof(R) == 4) - 4 * K;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int L = B > 1 ? tile_lat[tile] : 0;
@@ -475,7 +483,7 @@ __global__ void __launch_bounds__(NT, MinCtas<R, NT, V>::value) persistent_kerne
                                                         Consts<typename Lanes<R, V>::type> c) {
   __shared__ R e_ut[NT / 32][4];
   __shared__ R e_f[NT / 32][4];
-  __shared__ float2 gbuf[GhostSlots<R, NT, V>::value];
+  __shared__ __align__(16) float2 gbuf[GhostSlots<R, NT, V>::value];
   __shared__ long long s_next;
   __shared__ int s_go;
   constexpr int U = kUnitTiles;  // tiles per work unit
