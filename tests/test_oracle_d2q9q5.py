@@ -1,0 +1,243 @@
+"""Pins of the two-dimensional D2Q9-D2Q5 oracle against what the paper and the mathematics fix.
+
+The paper names the D2Q9-D2Q5 coupling without specifying it, so the pins check the readings through
+properties that do not depend on retyping them: exact reduction to the pinned one-dimensional D1Q3Q3
+oracle, textbook special cases, linear stability, decay rates from the second-order analysis of
+section 8 carried to two dimensions, lattice symmetries and conservation."""
+import numpy as np
+import pytest
+
+import oracle as O1
+import oracle.d2q9q5 as D
+
+
+def smooth_1d(N, seed):
+    rng = np.random.default_rng(seed)
+    x = 2 * np.pi * np.arange(N) / N
+    rho = 1.0 + 0.08 * np.sin(x + rng.uniform(0, 6)) + 0.03 * np.sin(2 * x + rng.uniform(0, 6))
+    u = 0.08 * np.sin(x + rng.uniform(0, 6)) + 0.02 * np.cos(3 * x)
+    s = 0.03 * np.cos(x + rng.uniform(0, 6))
+    return rho, u, s
+
+
+def smooth_2d(Ny, Nx, seed, amp=0.04):
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:Ny, 0:Nx]
+    X, Y = 2 * np.pi * xx / Nx, 2 * np.pi * yy / Ny
+    f = lambda: amp * (np.sin(X + rng.uniform(0, 6)) * np.cos(Y + rng.uniform(0, 6)) + 0.5 * np.sin(2 * Y + X + rng.uniform(0, 6)))
+    return 1.0 + f(), f(), f(), 0.5 * f()
+
+
+PHYS_CASES = [dict(), dict(gamma=1.3, Pr=0.71, cp=2.5, rho0=1.3, lam=2.0, s0=-0.1)]
+
+
+@pytest.mark.parametrize("kw", PHYS_CASES)
+def test_reduces_to_d1q3q3_on_one_dimensional_data(kw):
+    """With the coupling of eq. (lien-sigma-sigma) (beta = 3/2), data that do not depend on y and have
+    J_y = 0 evolve exactly as the D1Q3Q3 scheme of sections 6 and 8 along x: the sums of the 2-D
+    populations over c_y are the 1-D populations (and likewise along y), source included."""
+    ph1 = O1.default_phys(**kw)
+    ph2 = D.default_phys(beta=1.5, **kw)
+    N, rows, steps, s_e = 48, 3, 40, 1.25
+    rho, u, s = smooth_1d(N, 5)
+    lam, cp = ph1.lam, ph1.cp
+    u = u * lam
+    s = s * cp + ph1.s0
+    ref = O1.run(ph1, O1.coupled_rates(s_e, ph1.gamma, ph1.Pr), O1.init(ph1, rho, u, s=s), steps)
+    rt = D.rates(s_e, ph1.gamma, ph1.Pr, beta=1.5)
+    T = lambda a: np.tile(a, (rows, 1))
+    got = D.run(ph2, rt, D.init(ph2, T(rho), T(u), 0 * T(u), T(s)), steps)
+    cx, cy = D.CX, D.CY
+    red = np.stack([got[0][:, (cx == a) & (np.arange(14) < 9)].sum(1) for a in (0, 1, -1)] +
+                   [got[0][:, (cx == a) & (np.arange(14) >= 9)].sum(1) for a in (0, 1, -1)], axis=1)
+    assert np.abs(red - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2])
+    assert np.abs(D.moments(ph2, got)[..., 2]).max() <= 1e-15
+    # Along y: the transposed data.
+    got_y = D.run(ph2, rt, D.init(ph2, T(rho).T, 0 * T(u).T, T(u).T, T(s).T), steps)
+    red_y = np.stack([got_y[:, 0][:, (cy == a) & (np.arange(14) < 9)].sum(1) for a in (0, 1, -1)] +
+                     [got_y[:, 0][:, (cy == a) & (np.arange(14) >= 9)].sum(1) for a in (0, 1, -1)], axis=1)
+    assert np.abs(red_y - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+def test_isothermal_lattice_rest_state_has_the_textbook_weights():
+    """At rest with p0 = rho0 lambda^2 / 3 (lattice temperature lambda^2/3) the D2Q9 equilibrium is the
+    textbook one, weights 4/9, 1/9, 1/36 times rho; the D2Q5 rest state holds (1 - 2 a) zeta at rest
+    and a zeta / 2 on each moving velocity, a the second moment per direction."""
+    for rho0 in (1.0, 1.2):  # populations are scaled by rho0 as in eq. (M-d1q3q3)
+        ph = D.default_phys(rho0=rho0, p0=rho0 / 3.0)
+        fd = D.init(ph, np.full((3, 3), rho0), np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3)))[1, 1]
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        assert np.abs(fd[:9] - w).max() <= 1e-15
+    # At T = T0 (s = s0) the log T term vanishes: E_xx = E_yy = s p, so a = p0 / rho0 = 1/3.
+    ph = D.default_phys(p0=1.0 / 3.0, s0=0.2)
+    g = D.init(ph, np.full((3, 3), 1.0), np.zeros((3, 3)), np.zeros((3, 3)), np.full((3, 3), 0.2))[1, 1][9:]
+    a = 1.0 / 3.0
+    assert abs(g[0] - 0.2 * (1 - 2 * a)) <= 1e-15 and np.abs(g[1:] - 0.2 * a / 2).max() <= 1e-15
+
+
+def _collision_jacobian(ph, rt, eps=1e-7):
+    """d(one step)/d(populations) of a uniform rest state: streaming a uniform field is the identity."""
+    n = 3
+    z = np.zeros((n, n))
+    f0 = D.init(ph, z + 1.0, z, z, z)
+    base = D.run(ph, rt, f0, 1)[1, 1]
+    J = np.zeros((14, 14))
+    for j in range(14):
+        f = f0.copy()
+        f[..., j] += eps
+        J[:, j] = (D.run(ph, rt, f, 1)[1, 1] - base) / eps
+    return J
+
+
+def _max_growth(J):
+    worst = 0.0
+    for th in np.linspace(0, np.pi / 4, 7):
+        for k in np.linspace(0.1, np.pi * np.sqrt(2), 30):
+            ph_ = np.exp(-1j * (k * np.cos(th) * D.CX + k * np.sin(th) * D.CY))
+            worst = max(worst, np.abs(np.linalg.eigvals(ph_[:, None] * J)).max())
+    return worst
+
+
+def test_closure_of_section_8_is_unstable_on_d2q5_and_beta_9_2_is_stable():
+    """Linear stability at rest (von Neumann symbol from the oracle's own collision Jacobian): with
+    the 1-D closure (beta = 3/2) the D2Q5 entropy block grows by more than 3 per step at the
+    diagonal modes; with beta = 9/2 no mode grows, for s_e from 1 to 1.9."""
+    ph = D.default_phys(source_on=0, beta=1.5)
+    J = _collision_jacobian(ph, D.rates(1.2, beta=1.5))
+    assert _max_growth(J) > 3.0
+    ph_ = np.exp(-1j * (np.pi * D.CX + np.pi * D.CY))
+    assert np.abs(np.linalg.eigvals((ph_[:, None] * J)[9:, 9:])).max() > 3.0  # the entropy block
+    for s_e in (1.0, 1.2, 1.5, 1.9):
+        ph = D.default_phys(source_on=0)
+        assert _max_growth(_collision_jacobian(ph, D.rates(s_e))) <= 1.0 + 1e-6, s_e
+
+
+def _decay_rate(ph, rt, fd, proj, t1, t2):
+    a = D.run(ph, rt, fd, t1)
+    b = D.run(ph, rt, a, t2 - t1)
+    return -np.log(proj(D.moments(ph, b)) / proj(D.moments(ph, a))) / (t2 - t1)
+
+
+def test_shear_waves_decay_at_nu_over_3_along_the_axes_and_the_diagonal():
+    """Section 8 with theta_e ~ lambda^2 d J gives the viscous stress sigma_e dt theta; in two
+    dimensions q_eq = -lambda^2 J makes it isotropic with shear viscosity nu/3 (nu of eq.
+    nu-d1q3q3): a shear wave of wave vector k decays at (nu/3)|k|^2 whatever its direction."""
+    ph, rt, s_e = D.default_phys(), D.rates(1.2), 1.2
+    nu = (1.0 / s_e - 0.5) * ph.lam * ph.dx
+    N, A = 48, 1e-5
+    k = 2 * np.pi / N
+    yy, xx = np.mgrid[0:N, 0:N].astype(float)
+    one, zero = np.ones((N, N)), np.zeros((N, N))
+    w = np.sin(k * yy)
+    r_axis = _decay_rate(ph, rt, D.init(ph, one, A * w, zero, zero), lambda m: np.sum(m[..., 1] * w), 50, 250)
+    wd = np.sin(k * (xx + yy))
+    fd = D.init(ph, one, -A * wd / np.sqrt(2), A * wd / np.sqrt(2), zero)
+    r_diag = _decay_rate(ph, rt, fd, lambda m: np.sum((m[..., 2] - m[..., 1]) * wd), 50, 250)
+    assert abs(r_axis / (nu / 3 * k * k) - 1) <= 0.01
+    assert abs(r_diag / (nu / 3 * 2 * k * k) - 1) <= 0.01
+
+
+@pytest.mark.parametrize("beta", [1.5, 4.5])
+def test_entropy_mode_diffusivity(beta):
+    """An entropy mode at rest and uniform pressure diffuses at kappa/(rho0 c_p) + sigma_psi dt p0/rho0:
+    the section 8 flux kappa d log T plus the p d s term that section 8 neglects. Along x for both
+    couplings (1-D data), and along the diagonal for beta = 9/2 (the 1-D closure is unstable there).
+    Long waves (N = 96), so that the O(k^2) corrections and the weak sound the conduction launches
+    stay within the bound."""
+    ph, s_e = D.default_phys(beta=beta), 1.2
+    rt = D.rates(s_e, beta=beta)
+    sigma_e = 1.0 / s_e - 0.5
+    pred = sigma_e * ph.lam * ph.dx / ph.Pr + beta * ph.gamma / ph.Pr * sigma_e * (ph.dx / ph.lam) * ph.p0 / ph.rho0
+    N, B = 96, 1e-4
+    k = 2 * np.pi / N
+    cases = [("x", 3, k * k)] + ([("diagonal", N, 2 * k * k)] if beta == 4.5 else [])
+    for name, rows, kk in cases:
+        yy, xx = np.mgrid[0:rows, 0:N].astype(float)
+        phase = k * xx if name == "x" else k * (xx + yy)
+        s = B * np.sin(phase)
+        rho = ph.rho0 * np.exp(-s / ph.cp)  # uniform pressure
+        fd = D.init(ph, rho, 0 * s, 0 * s, s)
+        r = _decay_rate(ph, rt, fd, lambda m: np.sum(m[..., 3] / m[..., 0] * np.sin(phase)), 60, 200)
+        assert abs(r / (pred * kk) - 1) <= 0.025, (beta, name, r / kk, pred)
+
+
+def test_transverse_wave_is_carried_by_the_mean_flow():
+    """Galilean check of the nonlinear momentum flux rho u_x u_y (the xy equilibrium): a transverse
+    wave u_y = A sin(k x) in a uniform flow u_x = U translates at U (10 nodes in 200 steps at
+    U = 0.05) to within 1 %."""
+    ph, rt = D.default_phys(), D.rates(1.2)
+    N, U, A, T = 64, 0.05, 1e-4, 200
+    k = 2 * np.pi / N
+    xx = np.arange(N)[None, :] * np.ones((3, 1))
+    one = np.ones((3, N))
+    f = D.init(ph, one, U * one, A * np.sin(k * xx), 0 * one)
+    phase = lambda f: np.angle(np.sum(D.moments(ph, f)[0, :, 2] * np.exp(-1j * k * np.arange(N))))
+    d = phase(D.run(ph, rt, f, T)) - phase(f)
+    shift = -((d + np.pi) % (2 * np.pi) - np.pi) / k
+    assert abs(shift - U * T) <= 0.01 * U * T
+
+
+def _one_step_production(ph, G, g_s, n=7):
+    """zeta after one step with the source minus without it, at the centre node, for the linear fields
+    u = G x and s = g_s . x (centred differences are exact on linear fields)."""
+    c = n // 2
+    yy, xx = np.mgrid[0:n, 0:n].astype(float)
+    X, Y = xx - c, yy - c
+    ux, uy = G[0, 0] * X + G[0, 1] * Y, G[1, 0] * X + G[1, 1] * Y
+    s = g_s[0] * X + g_s[1] * Y
+    rho = np.ones((n, n)) * ph.rho0
+    off = D.default_phys(source_on=0)
+    rt = D.rates(1.2)
+    fd = D.init(ph, rho, ux, uy, s)
+    return D.moments(ph, D.run(ph, rt, fd, 1))[c, c, 3] - D.moments(off, D.run(off, rt, fd, 1))[c, c, 3]
+
+
+def test_entropy_production_is_rotation_invariant_and_reduces_to_one_dimension():
+    """The production rho nu (2 D:D + (div u)^2) / (3 T) + kappa |grad T|^2 / T^2 depends on the
+    velocity gradient only through rotation invariants: rotating a uniform gradient by 45 degrees
+    leaves it unchanged, and on a one-dimensional gradient it is rho nu (d_x u)^2 / T. The thermal part
+    alone is invariant too."""
+    ph = D.default_phys()
+    th = np.pi / 4
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    G = 0.004 * np.array([[0.3, -0.7], [0.2, 0.5]])
+    a, b = _one_step_production(ph, G, (0, 0)), _one_step_production(ph, R @ G @ R.T, (0, 0))
+    assert a > 0 and abs(a - b) <= 1e-10 * a
+    gs = 2e-3 * np.array([0.6, -0.3])
+    a, b = _one_step_production(ph, 0 * G, gs), _one_step_production(ph, 0 * G, R @ gs)
+    assert a > 0 and abs(a - b) <= 1e-3 * a  # T is not exactly linear in s: centred differences of T
+    # A pure shear d_y u_x = g gives 2 D:D + (div u)^2 = g^2, a dilatation d_x u_x = g gives 3 g^2.
+    shear = _one_step_production(ph, 0.004 * np.array([[0, 1.0], [0, 0]]), (0, 0))
+    dil = _one_step_production(ph, 0.004 * np.array([[1.0, 0], [0, 0]]), (0, 0))
+    assert abs(shear / dil - 1.0 / 3.0) <= 1e-6  # (2 * 1/2) / (2 + 1)
+
+
+def test_transposition_covariance():
+    """Swapping x and y (a symmetry of both lattices) commutes with the step."""
+    ph, rt = D.default_phys(), D.rates(1.3)
+    rho, ux, uy, s = smooth_2d(20, 24, 3)
+    a = D.run(ph, rt, D.init(ph, rho, ux, uy, s), 12)
+    b = D.run(ph, rt, D.init(ph, rho.T, uy.T, ux.T, s.T), 12)
+    ma, mb = D.moments(ph, a), D.moments(ph, b)
+    perm = [0, 2, 1, 3, 4, 5, 6, 8, 7, 9, 11, 10, 12, 13]
+    sign = np.array([1, 1, 1, 1, 1, -1, 1, 1, 1, 1, 1, 1, 1, -1])
+    assert np.abs(mb.transpose(1, 0, 2)[..., perm] * sign - ma).max() <= 1e-13
+
+
+def test_conservation_and_uniform_state():
+    """Mass and momentum are conserved exactly (periodic lattice); without the source so is sum zeta,
+    with it sum zeta grows; a uniform state in uniform motion is a fixed point of the collision and
+    is only translated."""
+    ph, rt = D.default_phys(), D.rates(1.2)
+    off = D.default_phys(source_on=0)
+    rho, ux, uy, s = smooth_2d(16, 18, 7, amp=0.06)
+    f0 = D.init(ph, rho, ux, uy, s)
+    m0 = D.moments(ph, f0).sum((0, 1))
+    m1 = D.moments(ph, D.run(ph, rt, f0, 30)).sum((0, 1))
+    m2 = D.moments(off, D.run(off, rt, f0, 30)).sum((0, 1))
+    assert np.abs(m1[:3] - m0[:3]).max() <= 1e-12 * np.abs(m0[0])
+    assert abs(m2[3] - m0[3]) <= 1e-12 * np.abs(m0[0]) and m1[3] > m0[3] + 1e-9
+    one = np.ones((5, 6))
+    f = D.init(ph, 1.1 * one, 0.05 * one, -0.03 * one, 0.02 * one)
+    assert np.abs(D.run(ph, rt, f, 3) - f).max() <= 1e-14

@@ -146,3 +146,41 @@ def test_d1q3_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_d1q3.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
+
+
+D2_SRC = os.path.join(ROOT, "oracle", "d2q9q5_oracle.cpp")
+
+D2_MUTANTS = {
+    "2d q_eq coefficient": ("eq[3] = -l2 * Jx;", "eq[3] = -0.5 * l2 * Jx;"),
+    "2d xi_eq sign": ("eq[9] = Exx - Eyy;", "eq[9] = Eyy - Exx;"),
+    "2d shear term factor": ("+ 0.5 * shear * shear;", "+ shear * shear;"),
+    "2d divergence term dropped": ("(2.0 * DD + div * div)", "(2.0 * DD)"),
+    "2d log T term ignores beta": ("(rho * ph.cp * l2 / (ph.gamma * ph.beta))",
+                                   "(2.0 * rho * ph.cp * l2 / (3.0 * ph.gamma))"),
+    "2d e_eq lattice term": ("eq[0] = 3.0 * (Pxx + Pyy) - 4.0 * l2 * rho;", "eq[0] = 3.0 * (Pxx + Pyy) - 2.0 * l2 * rho;"),
+    "2d h_eq drops 1/rho": ("9.0 * Pxx * Pyy / rho;", "9.0 * Pxx * Pyy;"),
+    "2d streaming against c_x": ("const int64_t xt = (x + CX[i] + Nx) % Nx", "const int64_t xt = (x - CX[i] + Nx) % Nx"),
+    "2d thermal term over T": ("kappa / (T * T) * (dxT * dxT + dyT * dyT)", "kappa / T * (dxT * dxT + dyT * dyT)"),
+    "2d nu drops lambda": ("const double nu = sigma_e * ph.lambda * ph.dx;", "const double nu = sigma_e * ph.dx;"),
+    "2d E_xx uses Pi_yy": ("const double Exx = s * Pxx + L, Eyy = s * Pyy + L;",
+                           "const double Exx = s * Pyy + L, Eyy = s * Pyy + L;"),
+    "2d psi_y uses u_x": ("eq[7] = zeta * uy;", "eq[7] = zeta * ux;"),
+    "2d M xy row": ("mm.M[6][j] = vx * vy;", "mm.M[6][j] = vx * vy * 0.5;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(D2_MUTANTS))
+def test_d2q9q5_pins_catch_planted_mistake(name, tmp_path):
+    old, new = D2_MUTANTS[name]
+    src = open(D2_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not found exactly once"
+    mut = tmp_path / "d2_mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libd2_mutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    "-o", str(lib), str(mut)], check=True)
+    env = dict(os.environ, D2Q9Q5_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_d2q9q5.py")],
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
