@@ -59,8 +59,8 @@ FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
 # 2,183,366,656 FMUL2) thread-instructions (no scalar FADD / FFMA / FMUL) over 17,477 x 512 x 8
 # node-steps = 821.0 (profiles/step_tiles_df_N8M.md).
 DF_FP32_OPS_PER_COMPUTED = 2 * (8805052416 + 18397548544 + 2183366656) / (17477 * 512 * 8)
-TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.41696e6 + 153.121792e6) / 8388608,
-                          ("f32", 8, 64, 4): (201.407744e6 + 153.624832e6) / 8388608,
+TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.492224e6 + 153.174272e6) / 8388608,
+                          ("f32", 8, 64, 4): (201.407232e6 + 153.744896e6) / 8388608,
                           ("f64", 1, 256, 2): (403.062016e6 + 347.52768e6) / 8388608}
 
 
@@ -484,7 +484,7 @@ def run_linear(args, lbm, torch):
 # (dram__bytes_read.sum + dram__bytes_write.sum of one persistent launch over 25 blocks of 8 steps, on
 # the batch selection at 1024 lattices, 33.8 M nodes: (20,723.5 + 20,387.7) MB / (33,783,937 x 25)),
 # keyed by (k, NT, V); profiles/persistent_vs_launch_batch256.md.
-BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20736.672768e6 + 20420.08576e6) / (33783937 * 25)}
+BATCH_TRAFFIC_BYTES_PER_NODE = {(8, 128, 4): (20729.632512e6 + 20420.880128e6) / (33783937 * 25)}
 # DRAM bytes of the backward sweep over its algorithmic bytes, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of every recompute and adjoint-block launch between the misfit seed and the
 # initial-state adjoint) on 256 x 65536 nodes (larger than L2), T = 64 (FP32, 4 reverse steps per
@@ -695,6 +695,49 @@ def run_d1q3(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
     return out
 
 
+# The two-dimensional D2Q9-D2Q5 scheme: 14 populations read and written once per node-update.
+D2_BYTES_PER_NODE = {"f32": 14 * 2 * 4, "f64": 14 * 2 * 8}
+# DRAM bytes per node-update of its step kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum of
+# one launch on a 4096 x 4096 lattice, scaled by the node count): profiles/step2d_kernel_4096.md.
+D2_TRAFFIC_BYTES_PER_NODE = {}
+
+
+def run_2d(args, lbm, torch, side: int, hbm_peak: float):
+    """The two-dimensional scheme on a periodic side x side lattice of smooth seeded waves (density,
+    velocity and entropy modes of relative amplitude 0.05), s_e = 1.2: one launch per step, timed on
+    the device as the other legs."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    fields = W.waves_2d(side, side, 2369, amp=0.05)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
+    del fields
+    N = side * side
+    out = {"lattice": f"{side} x {side} periodic", "workload": "seeded smooth waves, amplitude 0.05, s_e = 1.2, "
+                                                                "beta = 9/2"}
+    for prec in args.precisions.split(","):
+        steps = args.d2_steps_f64 if prec == "f64" else args.d2_steps_f32
+        lat = lbm.Lattice2D(side, side, precision=prec, s_e=S_E)
+        lat.set_state(*d)
+        ms = time_device(lat, torch, steps, 3, None, 1)
+        rho = lat.fields(device=True)[0]
+        finite = bool(torch.isfinite(rho).all().item())
+        del rho
+        lat.close()
+        glups = N * steps / (ms * 1e-3) / 1e9
+        launch_ms = ms / steps
+        achieved = N * D2_BYTES_PER_NODE[prec] / (launch_ms * 1e-3) / 1e9
+        tb = D2_TRAFFIC_BYTES_PER_NODE.get(prec)
+        out[prec] = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": 1, "launch_ms": launch_ms,
+                     "finite": finite,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved / hbm_peak, "traffic": None if tb is None else tb * N,
+                                  "algorithmic_bytes_per_launch": N * D2_BYTES_PER_NODE[prec]}}
+        torch.cuda.empty_cache()
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
 def oracle_accuracy(O, batched, sweep, cores: int):
     """The CPU leg's accuracy statements (the oracle as it stands, on bounded samples): L1(rho) of the
     ragged batch's shortest lattices after the timed 2000 steps, and of the precision sweep's three rates
@@ -763,6 +806,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
         if rank == 0:
             print(json.dumps({"profiling_case": True, "solver": "D1Q3 schemes", "nodes": args.nodes,
                               "results": res, "clocks": clk.summary()}), flush=True)
+        return
+    if args.d2_only:
+        with ClockSampler(local) as clk:
+            res = run_2d(args, lbm, torch, args.d2_side, hbm_peak)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "two-dimensional D2Q9-D2Q5", "results": res,
+                              "clocks": clk.summary()}), flush=True)
         return
     if args.fd_only:
         with ClockSampler(local) as clk:
@@ -851,6 +901,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     adjoint = None if args.no_adjoint else run_adjoint(args, lbm, torch, hbm_peak)
     fdiff = None if args.no_fd else run_fd(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
     d1q3 = None if args.no_d1q3 else run_d1q3(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
+    two_d = None if args.no_2d else run_2d(args, lbm, torch, args.d2_side, hbm_peak)
 
     if rank != 0:
         return
@@ -936,7 +987,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
                      "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
-            "finite_differences": fdiff, "d1q3_schemes": d1q3, "precision_sweep": sweep,
+            "finite_differences": fdiff, "d1q3_schemes": d1q3, "d2q9_d2q5": two_d, "precision_sweep": sweep,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"],
             "gpu_launches_note": "step-kernel launches per timed region of K lattice steps (K / steps per launch, "
                                  "rounded up: a remainder runs as one shorter launch)",
@@ -983,6 +1034,11 @@ def main():
     ap.add_argument("--d1q3-config", default="", help="k,block_threads,nodes_per_thread of the D1Q3 kernels")
     ap.add_argument("--d1q3-steps-f64", type=int, default=500)
     ap.add_argument("--d1q3-steps-f32", type=int, default=2000)
+    ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--d2-only", action="store_true", help="only the two-dimensional D2Q9-D2Q5 leg")
+    ap.add_argument("--d2-side", type=int, default=8192)
+    ap.add_argument("--d2-steps-f32", type=int, default=200)
+    ap.add_argument("--d2-steps-f64", type=int, default=20)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -391,6 +391,71 @@ int lbm_d1q3_get_config(const lbm_d1q3_ctx *ctx, int32_t *steps_per_launch, int3
  * buffer, over at most 16384 tiles) and keeps the fastest per node-update. Synchronises. */
 int lbm_d1q3_autotune(lbm_d1q3_ctx *ctx, int32_t trials);
 
+/* ---------------------------------------------------------------------------------------------
+ * Two-dimensional coupled D2Q9-D2Q5 scheme for (rho, J, zeta). The paper's conclusion names this
+ * coupling as the next step and specifies nothing more; the scheme here carries section 8 to two
+ * dimensions (the readings of the CPU reference): D2Q9 populations f0..f8 for the velocities
+ * lambda c, c = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1), D2Q5 populations g0..g4
+ * for c = (0,0) (1,0) (0,1) (-1,0) (0,-1), periodic in x and y.
+ *  - Moments (rows scaled by rho0, the entropy rows also by c_p, as in eq. M-d1q3q3): rho, J,
+ *    e = sum (3|v|^2 - 4 lambda^2) f, xx = sum (vx^2 - vy^2) f, xy = sum vx vy f,
+ *    q = sum (3|v|^2 - 5 lambda^2) v f, h = sum (4 lambda^4 - 21/2 lambda^2 |v|^2 + 9/2 |v|^4) f;
+ *    zeta, psi = c_p sum v g, eps = c_p sum (3|v|^2 - 4 lambda^2) g, xi = c_p sum (vx^2 - vy^2) g.
+ *  - Equilibria, with p(rho, s) of eq. (gaz-parfait), Pi = rho u u + p I and
+ *    E = s Pi + (rho c_p lambda^2 / (gamma beta)) log(T/T0) I: e_eq = 3 tr Pi - 4 lambda^2 rho,
+ *    xx_eq = Pi_xx - Pi_yy, xy_eq = Pi_xy, q_eq = -lambda^2 J, h_eq = 4 lambda^4 rho
+ *    - 6 lambda^2 tr Pi + 9 Pi_xx Pi_yy / rho, psi_eq = zeta u, eps_eq = 3 tr E - 4 lambda^2 zeta,
+ *    xi_eq = E_xx - E_yy.
+ *  - Rates: s_e (e, xx, xy), s_q, s_h, s_psi, s_eps (eps, xi); sigma_psi = beta (gamma/Pr) sigma_e.
+ *    beta = 3/2 (eq. lien-sigma-sigma) makes the scheme the D1Q3Q3 one on one-dimensional data but
+ *    leaves its D2Q5 part linearly unstable at the diagonal modes; the default is beta = 9/2.
+ *  - Production added to zeta after relaxation: dt [rho nu (2 D:D + (div u)^2) / (3T)
+ *    + kappa |grad T|^2 / T^2], nu = sigma_e lambda dx, kappa = rho nu c_p / Pr, centred
+ *    differences of u and T at time t; then streaming f_i(x + c_i dx) = f_i*(x).
+ * Storage: 14 planes of nx * ny values (x fastest), LBM_F64 or LBM_F32_SHIFTED (populations less
+ * those of the rest state rho0, u = 0, s0, in units of rho0). Same status codes and pointer
+ * conventions as the other schemes: arrays may be host or device memory. */
+typedef struct {
+  double gamma;   /* > 1 */
+  double Pr;      /* > 0 */
+  double cp;      /* > 0 */
+  double rho0;    /* > 0 */
+  double p0;      /* pressure at rho0, s0; <= 0 selects rho0 c0^2 / gamma with c0 = lambda / 2 */
+  double s0;      /* reference entropy */
+  double lambda;  /* > 0 */
+  double dx;      /* > 0 */
+  double beta;    /* coupling of sigma_psi; <= 0 selects 9/2 */
+  double s_e;     /* rate of e, xx, xy in (0, 2) */
+  double s_psi;   /* <= 0: from beta */
+  double s_eps;   /* <= 0 selects 1.5 */
+  double s_q;     /* <= 0 selects 1.5 */
+  double s_h;     /* <= 0 selects 1.5 */
+  int32_t source_on;
+  int32_t pad;
+} lbm2d_params;
+
+typedef struct lbm2d_ctx lbm2d_ctx;
+
+/* nx, ny >= 3 nodes, precision LBM_F64 or LBM_F32_SHIFTED. LBM_ERR_INVALID_ARG for a rate outside
+ * (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 14-plane state buffers cannot be had. */
+int lbm2d_create(lbm2d_ctx **out, int64_t nx, int64_t ny, const lbm2d_params *params, int32_t precision,
+                 void *stream);
+void lbm2d_destroy(lbm2d_ctx *ctx);
+const char *lbm2d_last_error(const lbm2d_ctx *ctx);
+int64_t lbm2d_steps_done(const lbm2d_ctx *ctx);
+/* The rates in use (s_e, s_psi, s_eps, s_q, s_h): host rates[5]. */
+int lbm2d_rates(const lbm2d_ctx *ctx, double *rates);
+/* Equilibrium state from the fields rho, ux, uy, s (float64 [ny][nx] each, host or device, all of
+ * one kind), computed in FP64 and stored rounded to the storage type. Resets the step counter. */
+int lbm2d_set_state(lbm2d_ctx *ctx, const double *rho, const double *ux, const double *uy, const double *s);
+/* Advances nsteps >= 0 time steps, one launch each (enqueued; no synchronisation). */
+int lbm2d_step(lbm2d_ctx *ctx, int64_t nsteps);
+/* Populations as float64, node-major [ny][nx][14] in the order (f0..f8, g0..g4), shift removed, in
+ * units of rho0 (the layout of the CPU reference); host or device. */
+int lbm2d_get_populations(lbm2d_ctx *ctx, double *f);
+/* The fields rho, ux, uy, s (float64 [ny][nx], host or device, any NULL). */
+int lbm2d_fields(lbm2d_ctx *ctx, double *rho, double *ux, double *uy, double *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,11 +37,12 @@ static inline cudaError_t take_bounds_record(unsigned long long out[3]) {
 #else
 __device__ __forceinline__ constexpr bool in_bounds(long long, long long) { return true; }
 #endif
-// Reads and clears the bounds record of lbm_step.cu, lbm_step_df.cu and lbm_adjoint.cu (zeros when the
-// build has no checks).
+// Reads and clears the bounds record of lbm_step.cu, lbm_step_df.cu, lbm_adjoint.cu and lbm2d.cu (zeros
+// when the build has no checks).
 cudaError_t bounds_record_step(unsigned long long out[3]);
 cudaError_t bounds_record_df(unsigned long long out[3]);
 cudaError_t bounds_record_adjoint(unsigned long long out[3]);
+cudaError_t bounds_record_2d(unsigned long long out[3]);
 
 // Per-lattice record on the device. tile0 is the index of the lattice's first tile for the current
 // tile width; chunk0 the index of its first diagnostics chunk.

@@ -71,6 +71,15 @@ class lbm_d1q3_params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("s_psi", ctypes.c_double), ("s_eps", ctypes.c_double)]
 
 
+class lbm2d_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("cp", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("p0", ctypes.c_double), ("s0", ctypes.c_double),
+                ("lam", ctypes.c_double), ("dx", ctypes.c_double), ("beta", ctypes.c_double),
+                ("s_e", ctypes.c_double), ("s_psi", ctypes.c_double), ("s_eps", ctypes.c_double),
+                ("s_q", ctypes.c_double), ("s_h", ctypes.c_double),
+                ("source_on", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -83,7 +92,7 @@ def header_functions() -> list[str]:
     """Names of the functions declared in include/lbm.h."""
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", txt)) - {"lbm_alloc_fn", "lbm_free_fn"})
+    return sorted(set(re.findall(r"\b(lbm(?:2d)?_[a-z_0-9]+)\s*\(", txt)) - {"lbm_alloc_fn", "lbm_free_fn"})
 
 
 def load_library(path: str = LIB_PATH):
@@ -157,6 +166,15 @@ def load_library(path: str = LIB_PATH):
             "lbm_d1q3_set_config": (i32, [vp, i32, i32, i32]),
             "lbm_d1q3_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
             "lbm_d1q3_autotune": (i32, [vp, i32]),
+            "lbm2d_create": (i32, [P(vp), i64, i64, P(lbm2d_params), i32, vp]),
+            "lbm2d_destroy": (None, [vp]),
+            "lbm2d_last_error": (ctypes.c_char_p, [vp]),
+            "lbm2d_steps_done": (i64, [vp]),
+            "lbm2d_rates": (i32, [vp, P(d)]),
+            "lbm2d_set_state": (i32, [vp, vp, vp, vp, vp]),
+            "lbm2d_step": (i32, [vp, i64]),
+            "lbm2d_get_populations": (i32, [vp, vp]),
+            "lbm2d_fields": (i32, [vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -638,3 +656,82 @@ class D1q3Lattice:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbm_d1q3_steps_done(self.ctx))
+
+
+class Lattice2D:
+    """Two-dimensional coupled D2Q9-D2Q5 scheme (lbm2d_* of the C-ABI) on a periodic nx x ny lattice;
+    precision "f64" or "f32". Fields are [ny, nx] arrays (x fastest); populations [ny, nx, 14] in the
+    order (f0..f8, g0..g4). Keyword parameters are the lbm2d_params fields (gamma, Pr, cp, rho0, p0,
+    s0, lam, dx, beta, s_e, s_psi, s_eps, s_q, s_h, source_on); the defaults are the section 9 values
+    with beta = 9/2."""
+
+    def __init__(self, nx: int, ny: int, precision: str = "f64", stream=None, **params):
+        torch = _torch()
+        self.lib = load_library()
+        install_torch_allocator()
+        base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, lam=1.0, dx=1.0, beta=0.0, s_e=1.2,
+                    s_psi=0.0, s_eps=0.0, s_q=0.0, s_h=0.0, source_on=1, pad=0)
+        unknown = set(params) - set(base)
+        if unknown:
+            raise TypeError(f"unknown lbm2d parameters {sorted(unknown)}")
+        base.update(params)
+        self.params = lbm2d_params(**base)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.nx, self.ny = int(nx), int(ny)
+        self.N = self.nx * self.ny
+        ctx = ctypes.c_void_p()
+        rc = self.lib.lbm2d_create(ctypes.byref(ctx), self.nx, self.ny, ctypes.byref(self.params),
+                                   PRECISIONS[precision], ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm2d_create failed")
+        self.ctx = ctx
+
+    def _check(self, rc: int, what: str):
+        if rc != LBM_OK:
+            raise LbmError(rc, f"{what}: {self.lib.lbm2d_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self):
+        r = (ctypes.c_double * 5)()
+        self._check(self.lib.lbm2d_rates(self.ctx, r), "lbm2d_rates")
+        return tuple(r)
+
+    def set_state(self, rho, ux, uy, s):
+        a = [_Arr(x, self.N) for x in (rho, ux, uy, s)]
+        self._check(self.lib.lbm2d_set_state(self.ctx, *(x.ptr for x in a)), "lbm2d_set_state")
+
+    def step(self, nsteps: int):
+        self._check(self.lib.lbm2d_step(self.ctx, int(nsteps)), "lbm2d_step")
+
+    def populations(self, device: bool = False):
+        torch = _torch()
+        n = 14 * self.N
+        out = torch.empty(n, dtype=torch.float64, device="cuda") if device else np.empty(n)
+        a = _Arr(out, n, writable=True)
+        self._check(self.lib.lbm2d_get_populations(self.ctx, a.ptr), "lbm2d_get_populations")
+        return out.reshape(self.ny, self.nx, 14)
+
+    def fields(self, device: bool = False):
+        """(rho, ux, uy, s), each [ny, nx]."""
+        torch = _torch()
+        if device:
+            out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(4)]
+        else:
+            out = [np.empty(self.N) for _ in range(4)]
+        a = [_Arr(x, self.N, writable=True) for x in out]
+        self._check(self.lib.lbm2d_fields(self.ctx, *(x.ptr for x in a)), "lbm2d_fields")
+        return tuple(x.reshape(self.ny, self.nx) for x in out)
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbm2d_steps_done(self.ctx))

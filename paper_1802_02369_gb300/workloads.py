@@ -96,6 +96,34 @@ class RaggedBatch:
         return self.rho[lo:hi], self.u[lo:hi], self.p[lo:hi]
 
 
+def waves_2d(nx: int, ny: int, seed: int, amp: float = 0.04, lam: float = 1.0, rho0: float = 1.0,
+             cp: float = 1.0, s0: float = 0.0, x0: int = 0, y0: int = 0, period=None):
+    """Smooth periodic two-dimensional fields (rho, ux, uy, s), each [ny, nx] with x fastest: a few
+    seeded Fourier modes of relative amplitude amp in density, velocity (units of lam) and entropy
+    (units of c_p, about s0). ``period`` = (Px, Py) evaluates the fields of a Px x Py periodic domain
+    on the window of nx x ny nodes starting at (x0, y0) (coordinates taken modulo the period), so that
+    a window of a large lattice can be regenerated alone."""
+    Px, Py = (nx, ny) if period is None else period
+    rng = np.random.default_rng(seed)
+    xs = (x0 + np.arange(nx)) % Px
+    ys = (y0 + np.arange(ny)) % Py
+    X = 2 * np.pi * xs[None, :] / Px
+    Y = 2 * np.pi * ys[:, None] / Py
+    modes = [(1, 0), (0, 1), (1, 1), (2, -1), (1, 2)]
+
+    def field():
+        out = np.zeros((ny, nx))
+        for kx, ky in modes:
+            a, ph = rng.uniform(-1, 1), rng.uniform(0, 2 * np.pi)
+            out = out + a * np.sin(kx * X + ky * Y + ph)
+        return amp * out / len(modes) ** 0.5
+
+    rho = rho0 * (1.0 + field())
+    ux, uy = lam * field(), lam * field()
+    s = s0 + cp * 0.5 * field()
+    return rho, ux, uy, s
+
+
 def entropy_of_state(rho, p_rel, gamma: float = 1.4, cp: float = 1.0, rho0: float = 1.0):
     """Specific entropy s - s0 of an ideal-gas state of density rho and pressure p_rel * p_unit,
     measured from the isentrope through (rho0, p_unit): (c_p / gamma) log(p_rel (rho0 / rho)^gamma).

@@ -21,7 +21,7 @@ def _declared():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
-        names |= set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", txt))
+        names |= set(re.findall(r"\b(lbm(?:2d)?_[a-z_0-9]+)\s*\(", txt))
     return sorted(names - {"lbm_alloc_fn", "lbm_free_fn"})
 
 
@@ -40,6 +40,7 @@ def test_binding_declares_the_same_functions(lib_path):
     assert lbm.header_functions() == _declared()
     for n in _declared():
         assert getattr(lib, n).argtypes is not None or n in ("lbm_destroy",)
+    assert any(n.startswith("lbm2d_") for n in _declared())
 
 
 def test_invalid_arguments_are_rejected_without_gpu(lib_path):
@@ -59,6 +60,18 @@ def test_invalid_arguments_are_rejected_without_gpu(lib_path):
     assert lib.lbm_create(ctypes.byref(ctx), 64, 1.0, ctypes.byref(bad), 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_total_nodes(None) == -1
+    # The two-dimensional scheme.
+    ok2 = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, lam=1.0, dx=1.0, beta=0.0, s_e=1.2,
+               s_psi=0.0, s_eps=0.0, s_q=0.0, s_h=0.0, source_on=1, pad=0)
+    for change in (dict(s_e=2.0), dict(gamma=1.0), dict(lam=0.0), dict(s_q=2.5), dict(rho0=-1.0), dict(Pr=0.0)):
+        p2 = lbm.lbm2d_params(**{**ok2, **change})
+        assert lib.lbm2d_create(ctypes.byref(ctx), 16, 16, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG, change
+    p2 = lbm.lbm2d_params(**ok2)
+    assert lib.lbm2d_create(ctypes.byref(ctx), 2, 16, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm2d_create(ctypes.byref(ctx), 16, 16, ctypes.byref(p2), 2, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm2d_create(ctypes.byref(ctx), 16, 4 * 65535 + 1, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm2d_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm2d_steps_done(None) == -1
 
 
 def test_noalloc_pointer_placement_rule(lib_path):
