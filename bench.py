@@ -61,6 +61,7 @@ FLOPS_PER_SM_CLOCK = {"f32": 256.0, "f64": 4.0}
 DF_FP32_OPS_PER_COMPUTED = 2 * (8805052416 + 18397548544 + 2183366656) / (17477 * 512 * 8)
 TRAFFIC_BYTES_PER_NODE = {("f32", 8, 128, 4): (201.492224e6 + 153.174272e6) / 8388608,
                           ("f32", 8, 64, 4): (201.407232e6 + 153.744896e6) / 8388608,
+                          ("f32", 8, 256, 4): (201.421568e6 + 152.067072e6) / 8388608,
                           ("f64", 1, 256, 2): (403.062016e6 + 347.52768e6) / 8388608}
 
 
@@ -699,7 +700,8 @@ def run_d1q3(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
 D2_BYTES_PER_NODE = {"f32": 14 * 2 * 4, "f64": 14 * 2 * 8}
 # DRAM bytes per node-update of its step kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum of
 # one launch on a 4096 x 4096 lattice, scaled by the node count): profiles/step2d_kernel_4096.md.
-D2_TRAFFIC_BYTES_PER_NODE = {}
+D2_TRAFFIC_BYTES_PER_NODE = {"f32": (940.501504e6 + 895.161344e6) / 16777216,
+                             "f64": (1882.121984e6 + 1831.835136e6) / 16777216}
 
 
 def run_2d(args, lbm, torch, side: int, hbm_peak: float):

@@ -56,10 +56,12 @@ __host__ __device__ P2T<R> lanes(const P2& p) {
   return t;
 }
 
-__device__ __forceinline__ float lg1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double lg1p(double x) { return log1p(x); }
-__device__ __forceinline__ float em1(float x) { return expm1f(x); }
-__device__ __forceinline__ double em1(double x) { return expm1(x); }
+// The logarithm and exponential are those of the one-dimensional kernels (lbm_internal.cuh): FP32
+// CUDA's log1pf / expm1f, FP64 the double-float series on the FP32 pipes. Reciprocals: FP32 a plain
+// division (the hardware estimate measured slower in this kernel), FP64 an FP32 estimate refined by
+// two FP64 Newton steps (the FP64 pipe bounds the FP64 kernel).
+__device__ __forceinline__ float rcp2d(float x) { return 1.0f / x; }
+__device__ __forceinline__ double rcp2d(double x) { return lbm::m_rcp(x); }
 
 // Conserved deviations of shifted populations.
 template <typename R>
@@ -86,12 +88,12 @@ struct Thermo {
 template <typename R>
 __device__ __forceinline__ Thermo<R> thermo(const Cons<R>& c, const P2T<R>& p) {
   Thermo<R> t;
-  t.inv = R(1) / (R(1) + c.r);
+  t.inv = rcp2d(R(1) + c.r);
   t.ux = c.jx * t.inv;
   t.uy = c.jy * t.inv;
   t.sig = (c.z - p.s0c * c.r) * t.inv;
-  t.lr = lg1p(c.r);
-  t.dP = p.P0 * em1(p.gamma * (t.lr + t.sig));
+  t.lr = lbm::m_log1p(c.r);
+  t.dP = p.P0 * lbm::m_expm1(p.gamma * (t.lr + t.sig));
   return t;
 }
 
@@ -173,12 +175,15 @@ __device__ __forceinline__ long long wrap(long long v, long long n) {
 // One time step of a 32 x TY tile: the tile and a halo of 2 nodes are read into shared memory with
 // their velocity and temperature deviation; the tile and a ring of 1 node collide (the production
 // needs the neighbours' u and T'); the tile pulls its populations from the collided neighbours.
-template <typename R, int TY>
+template <typename R, int TY, bool REUSE>
 __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ in, R* __restrict__ out, int nx, int ny,
                                                          long long plane, P2T<R> p) {
   constexpr int TX = 32, RX = TX + 4, RY = TY + 4, NR = RX * RY, NT = TX * TY;
   __shared__ R sf[kQ][NR];
-  __shared__ R su[NR], sv[NR], sT[NR];
+  // Per node: u, T' (the neighbours' values of the production) and the rest of the thermodynamic
+  // state, computed once for the tile and its halo and reused by the collision.
+  constexpr int NS = REUSE ? NR : 1;
+  __shared__ R su[NR], sv[NR], sT[NR], sinv[NS], ssig[NS], slr[NS], sdP[NS];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   for (int k = threadIdx.x; k < NR; k += NT) {
     const int ry = k / RX, rx = k - ry * RX;
@@ -195,6 +200,12 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ i
     su[k] = t.ux;
     sv[k] = t.uy;
     sT[k] = temp_dev(c, t, p);
+    if constexpr (REUSE) {
+      sinv[k] = t.inv;
+      ssig[k] = t.sig;
+      slr[k] = t.lr;
+      sdP[k] = t.dP;
+    }
   }
   __syncthreads();
   constexpr int IX = RX - 2, NI = IX * (RY - 2);
@@ -205,7 +216,20 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ i
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[i] = sf[i][n];
     Cons<R> c = conserved(f);
-    const Thermo<R> t = thermo(c, p);
+    const Thermo<R> t = [&]() {
+      if constexpr (REUSE) {
+        Thermo<R> k;
+        k.inv = sinv[n];
+        k.ux = su[n];
+        k.uy = sv[n];
+        k.sig = ssig[n];
+        k.lr = slr[n];
+        k.dP = sdP[n];
+        return k;
+      } else {
+        return thermo(c, p);
+      }
+    }();
     R m[10], eq[10];
     nonconserved(f, m);
     equilibria(c, t, p, eq);
@@ -219,7 +243,10 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ i
       const R shear = dyu + dxv, div = dxu + dyv;
       const R G = R(2) * (dxu * dxu + dyv * dyv) + shear * shear + div * div;  // 2 D:D + (div u)^2
       const R rho = R(1) + c.r, P = p.P0 + t.dP, Tn = R(1) + sT[n];
-      c.z = c.z + p.q_vis * rho * rho / P * G + p.q_th * rho * (dxT * dxT + dyT * dyT) / (Tn * Tn);
+      if constexpr (sizeof(R) == 4)
+        c.z = c.z + p.q_vis * rho * rho / P * G + p.q_th * rho * (dxT * dxT + dyT * dyT) / (Tn * Tn);
+      else
+        c.z = c.z + p.q_vis * rho * rho * rcp2d(P) * G + p.q_th * rho * (dxT * dxT + dyT * dyT) * rcp2d(Tn * Tn);
     }
     populations(c, m, f);
 #pragma unroll
@@ -369,8 +396,11 @@ int derive(const lbm2d_params* in, P2& p) {
 template <typename R>
 cudaError_t launch_step(lbm2d_ctx* c) {
   constexpr int TY = sizeof(R) == 4 ? 8 : 4;
+  // FP64 keeps the thermodynamic state of phase 1 for the collision (its logarithm, exponential and
+  // reciprocals load the FP64 pipe); FP32 recomputes it, measured faster.
+  constexpr bool REUSE = sizeof(R) == 8;
   const dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + TY - 1) / TY));
-  step2d_kernel<R, TY><<<grid, 32 * TY, 0, c->stream>>>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur],
+  step2d_kernel<R, TY, REUSE><<<grid, 32 * TY, 0, c->stream>>>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur],
                                                           (int)c->nx, (int)c->ny, c->n(), lanes<R>(c->p));
   return cudaGetLastError();
 }
