@@ -700,7 +700,7 @@ def run_d1q3(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
 D2_BYTES_PER_NODE = {"f32": 14 * 2 * 4, "f64": 14 * 2 * 8}
 # DRAM bytes per node-update of its step kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum of
 # one launch on a 4096 x 4096 lattice, scaled by the node count): profiles/step2d_kernel_4096.md.
-D2_TRAFFIC_BYTES_PER_NODE = {"f32": (940.501504e6 + 895.161344e6) / 16777216,
+D2_TRAFFIC_BYTES_PER_NODE = {"f32": (942.33984e6 + 895.275264e6) / 16777216,
                              "f64": (1882.121984e6 + 1831.835136e6) / 16777216}
 
 
