@@ -95,6 +95,13 @@ def test_source_off_and_rates(D, lbm):
     lat.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_long_horizon(D, lbm, precision, tol):
+    """500 steps on a 48 x 40 lattice: the errors stay within the same bounds."""
+    _, ref, pops, _ = run_both(D, lbm, 48, 40, 500, precision, {}, seed=13)
+    assert np.abs(pops - ref).max() <= tol
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_full_size_sampled_windows(D, lbm, precision):
     """A 4096 x 4096 lattice after 12 steps, compared on 16 x 16 windows: the oracle runs each window

@@ -241,3 +241,42 @@ def test_conservation_and_uniform_state():
     one = np.ones((5, 6))
     f = D.init(ph, 1.1 * one, 0.05 * one, -0.03 * one, 0.02 * one)
     assert np.abs(D.run(ph, rt, f, 3) - f).max() <= 1e-14
+
+
+def _moving_jacobian(ph, rt, ux, uy, s, eps=1e-7):
+    """The collision Jacobian about a uniform state in uniform motion (streaming it is the identity)."""
+    z = np.zeros((3, 3))
+    f0 = D.init(ph, z + ph.rho0, z + ux, z + uy, z + s)
+    base = D.run(ph, rt, f0, 1)[1, 1]
+    J = np.zeros((14, 14))
+    for j in range(14):
+        f = f0.copy()
+        f[..., j] += eps
+        J[:, j] = (D.run(ph, rt, f, 1)[1, 1] - base) / eps
+    return J
+
+
+def _growth_all_directions(J):
+    worst = 0.0  # the symbol at -k is the conjugate of the one at k: half the directions suffice
+    for th in np.linspace(0, np.pi, 12, endpoint=False):
+        for k in np.linspace(0.05, np.pi * np.sqrt(2), 24):
+            ph_ = np.exp(-1j * (k * np.cos(th) * D.CX + k * np.sin(th) * D.CY))
+            worst = max(worst, np.abs(np.linalg.eigvals(ph_[:, None] * J)).max())
+    return worst
+
+
+def test_stability_region_in_flow_and_entropy():
+    """Linear stability about uniform states of the two-dimensional scheme (beta = 9/2): stable in flow
+    up to |u| = 0.1 lambda along an axis and along the diagonal (s_e = 1.2 and 1.9) and at rest for
+    s - s0 = -0.1 and 0.1 c_p; growing for s - s0 = 0.2 c_p and, at s_e = 1.9, for |u| = 0.15 lambda:
+    close to the region of the one-dimensional scheme (tests/test_oracle_stability.py)."""
+    ph = D.default_phys(source_on=0)
+    for s_e in (1.2, 1.9):
+        rt = D.rates(s_e)
+        for ux, uy in ((0.1, 0.0), (0.1 / np.sqrt(2), 0.1 / np.sqrt(2))):
+            assert _growth_all_directions(_moving_jacobian(ph, rt, ux, uy, 0.0)) <= 1.0 + 1e-6, (s_e, ux, uy)
+    rt = D.rates(1.2)
+    for s in (-0.1, 0.1):
+        assert _growth_all_directions(_moving_jacobian(ph, rt, 0.0, 0.0, s)) <= 1.0 + 1e-6, s
+    assert _growth_all_directions(_moving_jacobian(ph, rt, 0.0, 0.0, 0.2)) > 1.2
+    assert _growth_all_directions(_moving_jacobian(ph, D.rates(1.9), 0.15, 0.0, 0.0)) > 1.005
