@@ -697,7 +697,7 @@ def run_d1q3(args, lbm, torch, N: int, hbm_peak: float, sm_clock_mhz: float):
 
 
 # The two-dimensional D2Q9-D2Q5 scheme: 14 populations read and written once per node-update.
-D2_BYTES_PER_NODE = {"f32": 14 * 2 * 4, "f64": 14 * 2 * 8}
+D2_BYTES_PER_NODE = {"f32": 14 * 2 * 4, "f64": 14 * 2 * 8, "f64df": 14 * 2 * 8}
 # DRAM bytes per node-update of its step kernel from ncu (dram__bytes_read.sum + dram__bytes_write.sum of
 # one launch on a 4096 x 4096 lattice, scaled by the node count): profiles/step2d_kernel_4096.md.
 D2_TRAFFIC_BYTES_PER_NODE = {"f32": (942.33984e6 + 895.275264e6) / 16777216,
@@ -716,8 +716,11 @@ def run_2d(args, lbm, torch, side: int, hbm_peak: float):
     N = side * side
     out = {"lattice": f"{side} x {side} periodic", "workload": "seeded smooth waves, amplitude 0.05, s_e = 1.2, "
                                                                 "beta = 9/2"}
-    for prec in args.precisions.split(","):
-        steps = args.d2_steps_f64 if prec == "f64" else args.d2_steps_f32
+    precs = args.precisions.split(",")
+    if "f64" in precs:
+        precs.append("f64df")  # FP64 planes, double-float arithmetic: FP64 accuracy on the FP32 pipes
+    for prec in precs:
+        steps = {"f64": args.d2_steps_f64, "f64df": args.d2_steps_f64df}.get(prec, args.d2_steps_f32)
         lat = lbm.Lattice2D(side, side, precision=prec, s_e=S_E)
         lat.set_state(*d)
         ms = time_device(lat, torch, steps, 3, None, 1)
@@ -1041,6 +1044,7 @@ def main():
     ap.add_argument("--d2-side", type=int, default=8192)
     ap.add_argument("--d2-steps-f32", type=int, default=200)
     ap.add_argument("--d2-steps-f64", type=int, default=20)
+    ap.add_argument("--d2-steps-f64df", type=int, default=40)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

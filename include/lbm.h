@@ -412,7 +412,7 @@ int lbm_d1q3_autotune(lbm_d1q3_ctx *ctx, int32_t trials);
  *  - Production added to zeta after relaxation: dt [rho nu (2 D:D + (div u)^2) / (3T)
  *    + kappa |grad T|^2 / T^2], nu = sigma_e lambda dx, kappa = rho nu c_p / Pr, centred
  *    differences of u and T at time t; then streaming f_i(x + c_i dx) = f_i*(x).
- * Storage: 14 planes of nx * ny values (x fastest), LBM_F64 or LBM_F32_SHIFTED (populations less
+ * Storage: 14 planes of nx * ny values (x fastest), LBM_F64 / LBM_F64_DF or LBM_F32_SHIFTED (populations less
  * those of the rest state rho0, u = 0, s0, in units of rho0). Same status codes and pointer
  * conventions as the other schemes: arrays may be host or device memory. */
 typedef struct {
@@ -436,7 +436,8 @@ typedef struct {
 
 typedef struct lbm2d_ctx lbm2d_ctx;
 
-/* nx, ny >= 3 nodes, precision LBM_F64 or LBM_F32_SHIFTED. LBM_ERR_INVALID_ARG for a rate outside
+/* nx, ny >= 3 nodes, precision LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (FP64 planes, the node update in
+ * double-float on the FP32 pipes, as for the one-dimensional scheme). LBM_ERR_INVALID_ARG for a rate outside
  * (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 14-plane state buffers cannot be had. */
 int lbm2d_create(lbm2d_ctx **out, int64_t nx, int64_t ny, const lbm2d_params *params, int32_t precision,
                  void *stream);

@@ -63,6 +63,34 @@ __host__ __device__ P2T<R> lanes(const P2& p) {
 __device__ __forceinline__ float rcp2d(float x) { return 1.0f / x; }
 __device__ __forceinline__ double rcp2d(double x) { return lbm::m_rcp(x); }
 
+// Double-float numbers for LBM_F64_DF: FP64 storage, the node update in double-float on the FP32 pipes
+// (the operations of lbm_df_core.cuh, about 48 significant bits), behind the operators the update is
+// written with. Construction from a double splits it into the nearest float and the remainder.
+struct dfn {
+  lbm::df v;
+  dfn() = default;
+  __host__ __device__ dfn(double x) : v(lbm::df_from_double_host(x)) {}
+  __device__ explicit dfn(lbm::df x) : v(x) {}
+};
+__device__ __forceinline__ dfn operator+(dfn a, dfn b) { return dfn(lbm::ad(a.v, b.v)); }
+__device__ __forceinline__ dfn operator-(dfn a, dfn b) { return dfn(lbm::sb(a.v, b.v)); }
+__device__ __forceinline__ dfn operator-(dfn a) { return dfn(lbm::df{-a.v.hi, -a.v.lo}); }
+__device__ __forceinline__ dfn operator*(dfn a, dfn b) { return dfn(lbm::ml(a.v, b.v)); }
+__device__ __forceinline__ dfn operator/(dfn a, dfn b) { return dfn(lbm::ml(a.v, lbm::m_rcp(b.v))); }
+__device__ __forceinline__ dfn rcp2d(dfn x) { return dfn(lbm::m_rcp(x.v)); }
+
+__device__ __forceinline__ float lg2d(float x) { return lbm::m_log1p(x); }
+__device__ __forceinline__ double lg2d(double x) { return lbm::m_log1p(x); }
+__device__ __forceinline__ dfn lg2d(dfn x) { return dfn(lbm::m_log1p(x.v)); }
+__device__ __forceinline__ float ex2d(float x) { return lbm::m_expm1(x); }
+__device__ __forceinline__ double ex2d(double x) { return lbm::m_expm1(x); }
+__device__ __forceinline__ dfn ex2d(dfn x) { return dfn(lbm::m_expm1(x.v)); }
+
+// Values as stored (FP32 or FP64 planes).
+__device__ __forceinline__ float stored(float x) { return x; }
+__device__ __forceinline__ double stored(double x) { return x; }
+__device__ __forceinline__ double stored(dfn x) { return lbm::to_double(x.v); }
+
 // Conserved deviations of shifted populations.
 template <typename R>
 struct Cons {
@@ -92,8 +120,8 @@ __device__ __forceinline__ Thermo<R> thermo(const Cons<R>& c, const P2T<R>& p) {
   t.ux = c.jx * t.inv;
   t.uy = c.jy * t.inv;
   t.sig = (c.z - p.s0c * c.r) * t.inv;
-  t.lr = lbm::m_log1p(c.r);
-  t.dP = p.P0 * lbm::m_expm1(p.gamma * (t.lr + t.sig));
+  t.lr = lg2d(c.r);
+  t.dP = p.P0 * ex2d(p.gamma * (t.lr + t.sig));
   return t;
 }
 
@@ -175,8 +203,9 @@ __device__ __forceinline__ long long wrap(long long v, long long n) {
 // One time step of a 32 x TY tile: the tile and a halo of 2 nodes are read into shared memory with
 // their velocity and temperature deviation; the tile and a ring of 1 node collide (the production
 // needs the neighbours' u and T'); the tile pulls its populations from the collided neighbours.
-template <typename R, int TY, bool REUSE>
-__global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ in, R* __restrict__ out, int nx, int ny,
+// S is the storage type of the planes, R the arithmetic (float, double, or dfn over double planes).
+template <typename S, typename R, int TY, bool REUSE>
+__global__ void __launch_bounds__(32 * TY) step2d_kernel(const S* __restrict__ in, S* __restrict__ out, int nx, int ny,
                                                          long long plane, P2T<R> p) {
   constexpr int TX = 32, RX = TX + 4, RY = TY + 4, NR = RX * RY, NT = TX * TY;
   __shared__ R sf[kQ][NR];
@@ -192,7 +221,7 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ i
     R f[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      f[i] = lbm::in_bounds(g + i * plane, kQ * plane) ? in[g + i * plane] : R(0);
+      f[i] = lbm::in_bounds(g + i * plane, kQ * plane) ? R(in[g + i * plane]) : R(0);
       sf[i][k] = f[i];
     }
     const Cons<R> c = conserved(f);
@@ -261,7 +290,7 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const R* __restrict__ i
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       const int src = n - c_cy[i] * RX - c_cx[i];
-      if (lbm::in_bounds(g + i * plane, kQ * plane) && lbm::in_bounds(src, NR)) out[g + i * plane] = sf[i][src];
+      if (lbm::in_bounds(g + i * plane, kQ * plane) && lbm::in_bounds(src, NR)) out[g + i * plane] = stored(sf[i][src]);
     }
   }
 }
@@ -326,7 +355,9 @@ struct lbm2d_ctx {
   long long steps_done = 0;
   std::string err;
   long long n() const { return nx * ny; }
-  size_t state_bytes() const { return (size_t)kQ * n() * (precision == LBM_F64 ? sizeof(double) : sizeof(float)); }
+  size_t state_bytes() const {
+    return (size_t)kQ * n() * (precision == LBM_F32_SHIFTED ? sizeof(float) : sizeof(double));
+  }
 };
 
 namespace {
@@ -393,16 +424,16 @@ int derive(const lbm2d_params* in, P2& p) {
   return LBM_OK;
 }
 
-template <typename R>
+template <typename S, typename R>
 cudaError_t launch_step(lbm2d_ctx* c) {
   // Tile heights measured at 8192 x 8192: FP32 8 / 12 / 16 rows 31.0 / 31.7 / 23.6 GLUPS (16 rows raise
   // the registers and halve the CTAs per SM); FP64 4 rows, the most that fits 48 KB of shared memory.
-  constexpr int TY = sizeof(R) == 4 ? 12 : 4;
+  constexpr int TY = sizeof(S) == 4 ? 12 : 4;
   // FP64 keeps the thermodynamic state of phase 1 for the collision (its logarithm, exponential and
   // reciprocals load the FP64 pipe); FP32 recomputes it, measured faster.
-  constexpr bool REUSE = sizeof(R) == 8;
+  constexpr bool REUSE = sizeof(S) == 8;
   const dim3 grid((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + TY - 1) / TY));
-  step2d_kernel<R, TY, REUSE><<<grid, 32 * TY, 0, c->stream>>>((const R*)c->state[c->cur], (R*)c->state[1 - c->cur],
+  step2d_kernel<S, R, TY, REUSE><<<grid, 32 * TY, 0, c->stream>>>((const S*)c->state[c->cur], (S*)c->state[1 - c->cur],
                                                           (int)c->nx, (int)c->ny, c->n(), lanes<R>(c->p));
   return cudaGetLastError();
 }
@@ -436,7 +467,7 @@ int lbm2d_create(lbm2d_ctx** out, int64_t nx, int64_t ny, const lbm2d_params* pa
   *out = nullptr;
   // ny / 4 tile rows must fit the grid's second dimension (65535).
   if (nx < 3 || ny < 3 || nx > (1LL << 30) || ny > 4LL * 65535 || nx * ny > (1LL << 34)) return LBM_ERR_INVALID_ARG;
-  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED) return LBM_ERR_INVALID_ARG;
+  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED && precision != LBM_F64_DF) return LBM_ERR_INVALID_ARG;
   P2 p{};
   if (int rc = derive(params, p)) return rc;
   lbm2d_ctx* c = new lbm2d_ctx();
@@ -496,7 +527,7 @@ int lbm2d_set_state(lbm2d_ctx* c, const double* rho, const double* ux, const dou
     d = c->d_stage + 2 * n;
     e = c->d_stage + 3 * n;
   }
-  if (c->precision == LBM_F64)
+  if (c->precision != LBM_F32_SHIFTED)
     init2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(a, b, d, e, (double*)c->state[c->cur], n, c->p);
   else
     init2d_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(a, b, d, e, (float*)c->state[c->cur], n, c->p);
@@ -513,7 +544,9 @@ int lbm2d_step(lbm2d_ctx* c, int64_t nsteps) {
   if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "lbm2d_step: nsteps < 0");
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "lbm2d_step: no state set");
   for (int64_t k = 0; k < nsteps; ++k) {
-    const cudaError_t e = c->precision == LBM_F64 ? launch_step<double>(c) : launch_step<float>(c);
+    const cudaError_t e = c->precision == LBM_F32_SHIFTED ? launch_step<float, float>(c)
+                          : c->precision == LBM_F64_DF   ? launch_step<double, dfn>(c)
+                                                         : launch_step<double, double>(c);
     if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("lbm2d step launch: ") + cudaGetErrorString(e));
     c->cur = 1 - c->cur;
     ++c->steps_done;
@@ -530,7 +563,7 @@ int lbm2d_get_populations(lbm2d_ctx* c, double* f) {
   if (host)
     if (int rc = ensure_stage(c)) return rc;
   double* d = host ? c->d_stage : f;
-  if (c->precision == LBM_F64)
+  if (c->precision != LBM_F32_SHIFTED)
     pops2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], d, n, c->p);
   else
     pops2d_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float*)c->state[c->cur], d, n, c->p);
@@ -556,7 +589,7 @@ int lbm2d_fields(lbm2d_ctx* c, double* rho, double* ux, double* uy, double* s) {
     if (int rc = ensure_stage(c)) return rc;
   double* d[4];
   for (int k = 0; k < 4; ++k) d[k] = outs[k] ? (host[k] ? c->d_stage + k * n : outs[k]) : nullptr;
-  if (c->precision == LBM_F64)
+  if (c->precision != LBM_F32_SHIFTED)
     fields2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->p, d[0],
                                                                          d[1], d[2], d[3]);
   else

@@ -68,7 +68,7 @@ def test_invalid_arguments_are_rejected_without_gpu(lib_path):
         assert lib.lbm2d_create(ctypes.byref(ctx), 16, 16, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG, change
     p2 = lbm.lbm2d_params(**ok2)
     assert lib.lbm2d_create(ctypes.byref(ctx), 2, 16, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG
-    assert lib.lbm2d_create(ctypes.byref(ctx), 16, 16, ctypes.byref(p2), 2, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm2d_create(ctypes.byref(ctx), 16, 16, ctypes.byref(p2), 3, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm2d_create(ctypes.byref(ctx), 16, 4 * 65535 + 1, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm2d_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm2d_steps_done(None) == -1

@@ -1,7 +1,7 @@
 """Parity of the two-dimensional D2Q9-D2Q5 kernel (through the C-ABI) with the FP64 CPU oracle.
 
-Populations are compared element by element in units of rho0: FP64 within 1e-12 (absolute; the
-populations are of order 0.1 to 1), FP32 within 1e-5 of the fields' scales (rho0, lambda, c_p) on
+Populations are compared element by element in units of rho0: FP64 and double-float within 1e-12
+(absolute; the populations are of order 0.1 to 1), FP32 within 1e-5 of the fields' scales (rho0, lambda, c_p) on
 rho, u, s and within 1e-5 on the populations."""
 import numpy as np
 import pytest
@@ -46,13 +46,14 @@ def run_both(D, lbm, nx, ny, steps, precision, kw, s_e=1.2, beta=4.5, seed=11, a
     return ph, ref, pops, got_fields
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64df"])
 @pytest.mark.parametrize("kw", PHYS)
 @pytest.mark.parametrize("shape", [(45, 37), (3, 3), (5, 70), (33, 4)])
-def test_fp64_populations_match_the_oracle(D, lbm, kw, shape):
+def test_fp64_populations_match_the_oracle(D, lbm, kw, shape, precision):
     """Ragged tile edges (45 x 37 on 32 x 4 tiles), lattices smaller than the tile and its halo (the
-    periodic wrap taken several times), non-default physics."""
+    periodic wrap taken several times), non-default physics; FP64 and double-float arithmetic."""
     nx, ny = shape
-    _, ref, pops, _ = run_both(D, lbm, nx, ny, 40, "f64", kw)
+    _, ref, pops, _ = run_both(D, lbm, nx, ny, 40, precision, kw)
     assert np.abs(pops - ref).max() <= 1e-12
 
 
@@ -95,14 +96,14 @@ def test_source_off_and_rates(D, lbm):
     lat.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f64df", 1e-12), ("f32", 1e-5)])
 def test_long_horizon(D, lbm, precision, tol):
     """500 steps on a 48 x 40 lattice: the errors stay within the same bounds."""
     _, ref, pops, _ = run_both(D, lbm, 48, 40, 500, precision, {}, seed=13)
     assert np.abs(pops - ref).max() <= tol
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f64df", "f32"])
 def test_full_size_sampled_windows(D, lbm, precision):
     """A 4096 x 4096 lattice after 12 steps, compared on 16 x 16 windows: the oracle runs each window
     with a halo of 2 nodes per step (the dependency radius of a step: streaming plus the centred
@@ -119,7 +120,7 @@ def test_full_size_sampled_windows(D, lbm, precision):
     ph = D.default_phys()
     rt = D.rates(1.2)
     h = 2 * T
-    tol = 1e-12 if precision == "f64" else 1e-5
+    tol = 1e-5 if precision == "f32" else 1e-12
     for (x0, y0) in [(0, 0), (N - 8, 1000), (2049, N - 9), (777, 3333)]:
         win = W.waves_2d(w + 2 * h, w + 2 * h, 23, amp=0.05, x0=x0 - h, y0=y0 - h, period=(N, N))
         ref = D.run(ph, rt, D.init(ph, *win), T)[h:h + w, h:h + w]
