@@ -184,3 +184,47 @@ def test_d2q9q5_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_d2q9q5.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
+
+
+D3_SRC = os.path.join(ROOT, "oracle", "d3q19q7_oracle.cpp")
+
+D3_MUTANTS = {
+    "3d q_eq coefficient": ("eq[6 + a] = -(2.0 / 3.0) * l2 * rho * u[a];", "eq[6 + a] = -l2 * rho * u[a];"),
+    "3d xiww sign": ("eq[20] = Eyy - Ezz;", "eq[20] = Ezz - Eyy;"),
+    "3d divergence term dropped": ("(2.0 * DD + div * div)", "(2.0 * DD)"),
+    "3d strain not symmetrised": ("const double D = 0.5 * (G[a][b] + G[b][a]);", "const double D = G[a][b];"),
+    "3d log T term ignores beta": ("(rho * ph.cp * l2 / (ph.gamma * ph.beta))",
+                                   "(2.0 * rho * ph.cp * l2 / (3.0 * ph.gamma))"),
+    "3d e_eq lattice term": ("eq[0] = 19.0 * tr - 30.0 * l2 * rho;", "eq[0] = 19.0 * tr - 20.0 * l2 * rho;"),
+    "3d Q4 drops 1/rho": ("const double Qxy = Pi[0][0] * Pi[1][1] / rho,", "const double Qxy = Pi[0][0] * Pi[1][1],"),
+    "3d pixx Q4_yz coefficient": ("+ 3.0 * (Qxy + Qxz) - 6.0 * Qyz;", "+ 3.0 * (Qxy + Qxz) - 3.0 * Qyz;"),
+    "3d streaming against c_z": ("zt = (z + CZ[i] + Nz) % Nz;", "zt = (z - CZ[i] + Nz) % Nz;"),
+    "3d y neighbour not wrapped": ("(z * Ny + (y == 0 ? Ny - 1 : y - 1)) * Nx + x", "(z * Ny + (y == 0 ? 0 : y - 1)) * Nx + x"),
+    "3d thermal term over T": ("kappa / (T * T) * gT2", "kappa / T * gT2"),
+    "3d nu drops lambda": ("const double nu = sigma_e * ph.lambda * ph.dx;", "const double nu = sigma_e * ph.dx;"),
+    "3d E_zz uses Pi_yy": ("Ezz = s * Pi[2][2] + L;", "Ezz = s * Pi[1][1] + L;"),
+    "3d psi_eq uses J": ("eq[15 + a] = zeta * u[a];", "eq[15 + a] = rho * u[a];"),
+    "3d M pyz row": ("mm.M[9][j] = l2 * cy * cz;", "mm.M[9][j] = l2 * cy * cz * 0.5;"),
+    "3d eps7 row orthogonal": ("mm.M[23][j] = ph.cp * l2 * (3.0 * c2 - 6.0);", "mm.M[23][j] = ph.cp * l2 * (7.0 * c2 - 6.0);"),
+    "3d psi relaxed with s_e": ("for (int k = 15; k < 18; ++k) rate[k] = rt.s_psi;",
+                                "for (int k = 15; k < 18; ++k) rate[k] = rt.s_e;"),
+    "3d entropy second moments relaxed with s_h": ("for (int k = 18; k < 21; ++k) rate[k] = rt.s_eps;",
+                                                   "for (int k = 18; k < 21; ++k) rate[k] = rt.s_h;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(D3_MUTANTS))
+def test_d3q19q7_pins_catch_planted_mistake(name, tmp_path):
+    old, new = D3_MUTANTS[name]
+    src = open(D3_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not found exactly once"
+    mut = tmp_path / "d3_mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libd3_mutant.so"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    "-o", str(lib), str(mut)], check=True)
+    env = dict(os.environ, D3Q19Q7_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_d3q19q7.py")],
+                       env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode != 0, f"pins did not catch the mutant {name!r}:\n{r.stdout[-2000:]}"
