@@ -743,6 +743,50 @@ def run_2d(args, lbm, torch, side: int, hbm_peak: float):
     return out
 
 
+# Algorithmic bytes of one node update of the three-dimensional scheme: 26 populations read and 26
+# written.
+D3_BYTES_PER_NODE = {"f32": 26 * 2 * 4, "f64": 26 * 2 * 8}
+# DRAM bytes per node per launch, read + write, from one ncu capture of step3d_kernel (none yet).
+D3_TRAFFIC_BYTES_PER_NODE = {}
+
+
+def run_3d(args, lbm, torch, side: int, hbm_peak: float):
+    """The three-dimensional scheme on a periodic side^3 lattice of smooth seeded waves (density and
+    velocity modes of relative amplitude 0.05, entropy 0.0125 c_p), s_e = 1.2: one launch per step,
+    timed on the device as the other legs."""
+    from paper_1802_02369_gb300 import workloads as W
+
+    fields = W.waves_3d(side, side, side, 2369, amp=0.05)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
+    del fields
+    N = side ** 3
+    out = {"lattice": f"{side} x {side} x {side} periodic",
+           "workload": "seeded smooth waves, amplitude 0.05, s_e = 1.2, beta = 9"}
+    for prec in args.precisions.split(","):
+        steps = args.d3_steps_f64 if prec == "f64" else args.d3_steps_f32
+        lat = lbm.Lattice3D(side, side, side, precision=prec, s_e=S_E)
+        lat.set_state(*d)
+        ms = time_device(lat, torch, steps, 3, None, 1)
+        rho = lat.fields(device=True)[0]
+        finite = bool(torch.isfinite(rho).all().item())
+        del rho
+        cfg = lat.get_config()
+        lat.close()
+        glups = N * steps / (ms * 1e-3) / 1e9
+        launch_ms = ms / steps
+        achieved = N * D3_BYTES_PER_NODE[prec] / (launch_ms * 1e-3) / 1e9
+        tb = D3_TRAFFIC_BYTES_PER_NODE.get(prec)
+        out[prec] = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": 1, "launch_ms": launch_ms,
+                     "finite": finite, "tile_rows": cfg[0], "keep": cfg[2],
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved / hbm_peak, "traffic": None if tb is None else tb * N,
+                                  "algorithmic_bytes_per_launch": N * D3_BYTES_PER_NODE[prec]}}
+        torch.cuda.empty_cache()
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
 def oracle_accuracy(O, batched, sweep, cores: int):
     """The CPU leg's accuracy statements (the oracle as it stands, on bounded samples): L1(rho) of the
     ragged batch's shortest lattices after the timed 2000 steps, and of the precision sweep's three rates
@@ -817,6 +861,13 @@ def run_ours(args, rank: int, world: int, local: int, dist):
             res = run_2d(args, lbm, torch, args.d2_side, hbm_peak)
         if rank == 0:
             print(json.dumps({"profiling_case": True, "solver": "two-dimensional D2Q9-D2Q5", "results": res,
+                              "clocks": clk.summary()}), flush=True)
+        return
+    if args.d3_only:
+        with ClockSampler(local) as clk:
+            res = run_3d(args, lbm, torch, args.d3_side, hbm_peak)
+        if rank == 0:
+            print(json.dumps({"profiling_case": True, "solver": "three-dimensional D3Q19-D3Q7", "results": res,
                               "clocks": clk.summary()}), flush=True)
         return
     if args.fd_only:
@@ -907,6 +958,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
     fdiff = None if args.no_fd else run_fd(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
     d1q3 = None if args.no_d1q3 else run_d1q3(args, lbm, torch, N_NODES, hbm_peak, clocks.get("sm_max_mhz") or 2070.0)
     two_d = None if args.no_2d else run_2d(args, lbm, torch, args.d2_side, hbm_peak)
+    three_d = None if args.no_3d else run_3d(args, lbm, torch, args.d3_side, hbm_peak)
 
     if rank != 0:
         return
@@ -992,7 +1044,7 @@ def run_ours(args, rank: int, world: int, local: int, dist):
                      "nodes_per_thread": f64["nodes_per_thread"], "roofline": roof_alu(f64, "f64"),
                      "roofline_hbm": roof(f64, "f64")},
             "batched_fp32": batched, "adjoint": adjoint, "linear_variant": linear,
-            "finite_differences": fdiff, "d1q3_schemes": d1q3, "d2q9_d2q5": two_d, "precision_sweep": sweep,
+            "finite_differences": fdiff, "d1q3_schemes": d1q3, "d2q9_d2q5": two_d, "d3q19_d3q7": three_d, "precision_sweep": sweep,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": f32["launches"],
             "gpu_launches_note": "step-kernel launches per timed region of K lattice steps (K / steps per launch, "
                                  "rounded up: a remainder runs as one shorter launch)",
@@ -1045,6 +1097,11 @@ def main():
     ap.add_argument("--d2-steps-f32", type=int, default=200)
     ap.add_argument("--d2-steps-f64", type=int, default=20)
     ap.add_argument("--d2-steps-f64df", type=int, default=40)
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--d3-only", action="store_true", help="only the three-dimensional D3Q19-D3Q7 leg")
+    ap.add_argument("--d3-side", type=int, default=256)
+    ap.add_argument("--d3-steps-f32", type=int, default=100)
+    ap.add_argument("--d3-steps-f64", type=int, default=10)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

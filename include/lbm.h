@@ -457,6 +457,88 @@ int lbm2d_get_populations(lbm2d_ctx *ctx, double *f);
 /* The fields rho, ux, uy, s (float64 [ny][nx], host or device, any NULL). */
 int lbm2d_fields(lbm2d_ctx *ctx, double *rho, double *ux, double *uy, double *s);
 
+/* ---------------------------------------------------------------------------------------------
+ * Three-dimensional coupled D3Q19-D3Q7 scheme for (rho, J, zeta): the second extension the paper's
+ * conclusion names, specified nowhere in it; the readings are those of the two-dimensional scheme
+ * carried to three dimensions. D3Q19 populations f0..f18 for the velocities lambda c,
+ * c = 0; (+-1,0,0) (0,+-1,0) (0,0,+-1) in that order; (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
+ * (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1); D3Q7 populations g0..g6
+ * for c = 0; (+-1,0,0) (0,+-1,0) (0,0,+-1); periodic in x, y and z.
+ *  - Moments (rows scaled by rho0, the entropy rows also by c_p; |c|^2 = c.c, each pattern times
+ *    lambda^k for its degree k): rho, J; e = 19|c|^2 - 30, pxx = 3cx^2 - |c|^2, pww = cy^2 - cz^2,
+ *    pxy, pyz, pxz = cx cy, cy cz, cx cz; q = (5|c|^2 - 9) c; mx, my, mz = (cy^2 - cz^2) cx,
+ *    (cz^2 - cx^2) cy, (cx^2 - cy^2) cz; eps = (21|c|^4 - 53|c|^2 + 24)/2, pixx = (3|c|^2 - 5)
+ *    (3cx^2 - |c|^2), piww = (3|c|^2 - 5)(cy^2 - cz^2); zeta, psi = c, eps7 = 3|c|^2 - 6 (the
+ *    one-dimensional row 3|c|^2 - 2d with d = 3), xixx = 3cx^2 - |c|^2, xiww = cy^2 - cz^2.
+ *  - Equilibria, with p(rho, s) of eq. (gaz-parfait), Pi = rho u u + p I, Q_ab = Pi_aa Pi_bb / rho and
+ *    E = s Pi + (rho c_p lambda^2 / (gamma beta)) log(T/T0) I: e = 19 tr Pi - 30 lambda^2 rho,
+ *    pxx = 3 Pi_xx - tr Pi, pww = Pi_yy - Pi_zz, pab = Pi_ab, q = -(2/3) lambda^2 J, m = 0,
+ *    eps = 12 lambda^4 rho - 16 lambda^2 tr Pi + 21 (Q_xy + Q_yz + Q_xz), pixx = 2 lambda^2 (tr Pi
+ *    - 3 Pi_xx) + 3 (Q_xy + Q_xz) - 6 Q_yz, piww = -2 lambda^2 (Pi_yy - Pi_zz) + 3 (Q_xy - Q_xz),
+ *    psi = zeta u, eps7 = 3 tr E - 6 lambda^2 zeta, xixx = 3 E_xx - tr E, xiww = E_yy - E_zz.
+ *  - Rates: s_e (e and the five second-order deviators), s_q (q, m), s_h (eps, pixx, piww), s_psi,
+ *    s_eps (eps7, xixx, xiww); sigma_psi = beta (gamma/Pr) sigma_e. beta = 3/2 (eq. lien-sigma-sigma)
+ *    makes the scheme the D1Q3Q3 one on one-dimensional data along any axis but leaves its D3Q7
+ *    part linearly unstable; the default is beta = 9, with s_q = 1.5, s_h = 1.2, s_eps = 1.0
+ *    (linearly stable at rest for s_e up to 1.5 and s - s0 up to 0.05 c_p).
+ *  - Production added to zeta after relaxation: dt [rho nu (2 D:D + (div u)^2) / (3T)
+ *    + kappa |grad T|^2 / T^2], nu = sigma_e lambda dx, kappa = rho nu c_p / Pr, centred
+ *    differences of u and T at time t; then streaming f_i(x + c_i dx) = f_i*(x).
+ * Storage: 26 planes of nx * ny * nz values (x fastest, then y, then z), LBM_F64 or LBM_F32_SHIFTED
+ * (populations less those of the rest state rho0, u = 0, s0, in units of rho0). Same status codes
+ * and pointer conventions as the other schemes: arrays may be host or device memory. */
+typedef struct {
+  double gamma;   /* > 1 */
+  double Pr;      /* > 0 */
+  double cp;      /* > 0 */
+  double rho0;    /* > 0 */
+  double p0;      /* pressure at rho0, s0; <= 0 selects rho0 c0^2 / gamma with c0 = lambda / 2 */
+  double s0;      /* reference entropy */
+  double lambda;  /* > 0 */
+  double dx;      /* > 0 */
+  double beta;    /* coupling of sigma_psi; <= 0 selects 9 */
+  double s_e;     /* rate of e and the second-order deviators, in (0, 2) */
+  double s_psi;   /* <= 0: from beta */
+  double s_eps;   /* <= 0 selects 1.0 */
+  double s_q;     /* <= 0 selects 1.5 */
+  double s_h;     /* <= 0 selects 1.2 */
+  int32_t source_on;
+  int32_t pad;
+} lbm3d_params;
+
+typedef struct lbm3d_ctx lbm3d_ctx;
+
+/* nx, ny, nz >= 3 nodes (nx up to 2^30, ny up to 4 * 65535, nx ny nz up to 2^33), precision
+ * LBM_F64 or LBM_F32_SHIFTED. LBM_ERR_INVALID_ARG for another precision, a size out of range, a rate
+ * outside (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 26-plane state buffers cannot be
+ * had. */
+int lbm3d_create(lbm3d_ctx **out, int64_t nx, int64_t ny, int64_t nz, const lbm3d_params *params,
+                 int32_t precision, void *stream);
+void lbm3d_destroy(lbm3d_ctx *ctx);
+const char *lbm3d_last_error(const lbm3d_ctx *ctx);
+int64_t lbm3d_steps_done(const lbm3d_ctx *ctx);
+/* The rates in use (s_e, s_psi, s_eps, s_q, s_h): host rates[5]. */
+int lbm3d_rates(const lbm3d_ctx *ctx, double *rates);
+/* Equilibrium state from the fields rho, ux, uy, uz, s (float64 [nz][ny][nx] each, host or device, all
+ * of one kind), computed in FP64 and stored rounded to the storage type. Resets the step counter. */
+int lbm3d_set_state(lbm3d_ctx *ctx, const double *rho, const double *ux, const double *uy, const double *uz,
+                    const double *s);
+/* Advances nsteps >= 0 time steps, one launch each (enqueued; no synchronisation). */
+int lbm3d_step(lbm3d_ctx *ctx, int64_t nsteps);
+/* Populations as float64, node-major [nz][ny][nx][26] in the order (f0..f18, g0..g6), shift removed, in
+ * units of rho0 (the layout of the CPU reference); host or device. */
+int lbm3d_get_populations(lbm3d_ctx *ctx, double *f);
+/* The fields rho, ux, uy, uz, s (float64 [nz][ny][nx], host or device, any NULL). */
+int lbm3d_fields(lbm3d_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *s);
+/* Kernel configuration: tile rows ty in {4, 8}, or 16 for FP32 (tiles of 32 x ty columns); the number
+ * of planes each CTA marches through along z (zc >= 1, capped at nz); keep = 1 holds a plane's
+ * populations in registers across the kernel's barrier, 0 reads them again after it (fewer
+ * registers, more CTAs per SM). 0 keeps the current ty or zc, -1 the current keep. Defaults: FP32
+ * 8 rows, FP64 4 rows, keep 0, zc from the lattice so that the grid fills the GPU about four times.
+ * Every configuration gives the same results bit for bit. */
+int lbm3d_set_config(lbm3d_ctx *ctx, int32_t ty, int32_t zc, int32_t keep);
+int lbm3d_get_config(const lbm3d_ctx *ctx, int32_t *ty, int32_t *zc, int32_t *keep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1122,9 +1122,10 @@ int lbm_debug_bounds(int64_t* violations, int64_t* first_index, int64_t* first_e
   if (!violations || !first_index || !first_extent) return LBM_ERR_INVALID_ARG;
 #ifdef LBM_DEBUG_BOUNDS
   if (cudaDeviceSynchronize() != cudaSuccess) return LBM_ERR_CUDA;
-  unsigned long long rec[4][3];
+  unsigned long long rec[5][3];
   if (lbm::bounds_record_step(rec[0]) != cudaSuccess || lbm::bounds_record_df(rec[1]) != cudaSuccess ||
-      lbm::bounds_record_adjoint(rec[2]) != cudaSuccess || lbm::bounds_record_2d(rec[3]) != cudaSuccess)
+      lbm::bounds_record_adjoint(rec[2]) != cudaSuccess || lbm::bounds_record_2d(rec[3]) != cudaSuccess ||
+      lbm::bounds_record_3d(rec[4]) != cudaSuccess)
     return LBM_ERR_CUDA;
   *violations = 0;
   *first_index = *first_extent = -1;

@@ -43,6 +43,7 @@ cudaError_t bounds_record_step(unsigned long long out[3]);
 cudaError_t bounds_record_df(unsigned long long out[3]);
 cudaError_t bounds_record_adjoint(unsigned long long out[3]);
 cudaError_t bounds_record_2d(unsigned long long out[3]);
+cudaError_t bounds_record_3d(unsigned long long out[3]);
 
 // Per-lattice record on the device. tile0 is the index of the lattice's first tile for the current
 // tile width; chunk0 the index of its first diagnostics chunk.

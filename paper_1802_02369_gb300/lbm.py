@@ -80,6 +80,10 @@ class lbm2d_params(ctypes.Structure):
                 ("source_on", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class lbm3d_params(ctypes.Structure):
+    _fields_ = lbm2d_params._fields_
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -92,7 +96,7 @@ def header_functions() -> list[str]:
     """Names of the functions declared in include/lbm.h."""
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm(?:2d)?_[a-z_0-9]+)\s*\(", txt)) - {"lbm_alloc_fn", "lbm_free_fn"})
+    return sorted(set(re.findall(r"\b(lbm(?:[23]d)?_[a-z_0-9]+)\s*\(", txt)) - {"lbm_alloc_fn", "lbm_free_fn"})
 
 
 def load_library(path: str = LIB_PATH):
@@ -175,6 +179,17 @@ def load_library(path: str = LIB_PATH):
             "lbm2d_step": (i32, [vp, i64]),
             "lbm2d_get_populations": (i32, [vp, vp]),
             "lbm2d_fields": (i32, [vp, vp, vp, vp, vp]),
+            "lbm3d_create": (i32, [P(vp), i64, i64, i64, P(lbm3d_params), i32, vp]),
+            "lbm3d_destroy": (None, [vp]),
+            "lbm3d_last_error": (ctypes.c_char_p, [vp]),
+            "lbm3d_steps_done": (i64, [vp]),
+            "lbm3d_rates": (i32, [vp, P(d)]),
+            "lbm3d_set_state": (i32, [vp, vp, vp, vp, vp, vp]),
+            "lbm3d_step": (i32, [vp, i64]),
+            "lbm3d_get_populations": (i32, [vp, vp]),
+            "lbm3d_fields": (i32, [vp, vp, vp, vp, vp, vp]),
+            "lbm3d_set_config": (i32, [vp, i32, i32, i32]),
+            "lbm3d_get_config": (i32, [vp, P(i32), P(i32), P(i32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -735,3 +750,91 @@ class Lattice2D:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbm2d_steps_done(self.ctx))
+
+
+class Lattice3D:
+    """Three-dimensional coupled D3Q19-D3Q7 scheme (lbm3d_* of the C-ABI) on a periodic nx x ny x nz
+    lattice; precision "f64" or "f32". Fields are [nz, ny, nx] arrays (x fastest); populations
+    [nz, ny, nx, 26] in the order (f0..f18, g0..g6). Keyword parameters are the lbm3d_params fields
+    (gamma, Pr, cp, rho0, p0, s0, lam, dx, beta, s_e, s_psi, s_eps, s_q, s_h, source_on); the defaults
+    are the section 9 values with beta = 9, s_q = 1.5, s_h = 1.2, s_eps = 1."""
+
+    def __init__(self, nx: int, ny: int, nz: int, precision: str = "f64", stream=None, **params):
+        torch = _torch()
+        self.lib = load_library()
+        install_torch_allocator()
+        base = dict(gamma=1.4, Pr=1.0, cp=1.0, rho0=1.0, p0=0.0, s0=0.0, lam=1.0, dx=1.0, beta=0.0, s_e=1.2,
+                    s_psi=0.0, s_eps=0.0, s_q=0.0, s_h=0.0, source_on=1, pad=0)
+        unknown = set(params) - set(base)
+        if unknown:
+            raise TypeError(f"unknown lbm3d parameters {sorted(unknown)}")
+        base.update(params)
+        self.params = lbm3d_params(**base)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        ctx = ctypes.c_void_p()
+        rc = self.lib.lbm3d_create(ctypes.byref(ctx), self.nx, self.ny, self.nz, ctypes.byref(self.params),
+                                   PRECISIONS[precision], ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm3d_create failed")
+        self.ctx = ctx
+
+    def _check(self, rc: int, what: str):
+        if rc != LBM_OK:
+            raise LbmError(rc, f"{what}: {self.lib.lbm3d_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm3d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rates(self):
+        r = (ctypes.c_double * 5)()
+        self._check(self.lib.lbm3d_rates(self.ctx, r), "lbm3d_rates")
+        return tuple(r)
+
+    def set_config(self, ty: int = 0, zc: int = 0, keep: int = -1):
+        self._check(self.lib.lbm3d_set_config(self.ctx, int(ty), int(zc), int(keep)), "lbm3d_set_config")
+
+    def get_config(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.lbm3d_get_config(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                    "lbm3d_get_config")
+        return a.value, b.value, c.value
+
+    def set_state(self, rho, ux, uy, uz, s):
+        a = [_Arr(x, self.N) for x in (rho, ux, uy, uz, s)]
+        self._check(self.lib.lbm3d_set_state(self.ctx, *(x.ptr for x in a)), "lbm3d_set_state")
+
+    def step(self, nsteps: int):
+        self._check(self.lib.lbm3d_step(self.ctx, int(nsteps)), "lbm3d_step")
+
+    def populations(self, device: bool = False):
+        torch = _torch()
+        n = 26 * self.N
+        out = torch.empty(n, dtype=torch.float64, device="cuda") if device else np.empty(n)
+        a = _Arr(out, n, writable=True)
+        self._check(self.lib.lbm3d_get_populations(self.ctx, a.ptr), "lbm3d_get_populations")
+        return out.reshape(self.nz, self.ny, self.nx, 26)
+
+    def fields(self, device: bool = False):
+        """(rho, ux, uy, uz, s), each [nz, ny, nx]."""
+        torch = _torch()
+        if device:
+            out = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(5)]
+        else:
+            out = [np.empty(self.N) for _ in range(5)]
+        a = [_Arr(x, self.N, writable=True) for x in out]
+        self._check(self.lib.lbm3d_fields(self.ctx, *(x.ptr for x in a)), "lbm3d_fields")
+        return tuple(x.reshape(self.nz, self.ny, self.nx) for x in out)
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbm3d_steps_done(self.ctx))

@@ -124,6 +124,35 @@ def waves_2d(nx: int, ny: int, seed: int, amp: float = 0.04, lam: float = 1.0, r
     return rho, ux, uy, s
 
 
+def waves_3d(nx: int, ny: int, nz: int, seed: int, amp: float = 0.04, lam: float = 1.0, rho0: float = 1.0,
+             cp: float = 1.0, s0: float = 0.0, x0: int = 0, y0: int = 0, z0: int = 0, period=None):
+    """Smooth periodic three-dimensional fields (rho, ux, uy, uz, s), each [nz, ny, nx] with x fastest:
+    a few seeded Fourier modes of relative amplitude amp in density, velocity (units of lam) and
+    entropy (units of c_p, about s0, at a quarter of amp: the three-dimensional scheme is linearly
+    stable for s - s0 up to about 0.05 c_p). ``period`` = (Px, Py, Pz) evaluates the fields of a
+    periodic domain on the window of nx x ny x nz nodes starting at (x0, y0, z0), so that a window of a
+    large lattice can be regenerated alone."""
+    Px, Py, Pz = (nx, ny, nz) if period is None else period
+    rng = np.random.default_rng(seed)
+    X = 2 * np.pi * ((x0 + np.arange(nx)) % Px)[None, None, :] / Px
+    Y = 2 * np.pi * ((y0 + np.arange(ny)) % Py)[None, :, None] / Py
+    Z = 2 * np.pi * ((z0 + np.arange(nz)) % Pz)[:, None, None] / Pz
+    modes = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, -1), (1, -2, 1)]
+
+    def field():
+        out = np.zeros((nz, ny, nx))
+        for kx, ky, kz in modes:
+            a, ph = rng.uniform(-1, 1), rng.uniform(0, 2 * np.pi)
+            out += a * np.sin(kx * X + ky * Y + kz * Z + ph)
+        out *= amp / len(modes) ** 0.5
+        return out
+
+    rho = rho0 * (1.0 + field())
+    ux, uy, uz = lam * field(), lam * field(), lam * field()
+    s = s0 + cp * 0.25 * field()
+    return rho, ux, uy, uz, s
+
+
 def entropy_of_state(rho, p_rel, gamma: float = 1.4, cp: float = 1.0, rho0: float = 1.0):
     """Specific entropy s - s0 of an ideal-gas state of density rho and pressure p_rel * p_unit,
     measured from the isentrope through (rho0, p_unit): (c_p / gamma) log(p_rel (rho0 / rho)^gamma).

@@ -1,10 +1,10 @@
 """The bounds-checked debug build: the library compiled with -DLBM_DEBUG_BOUNDS checks every global and
-shared-memory index of the step, persistent, double-float, adjoint and two-dimensional kernels before
+shared-memory index of the step, persistent, double-float, adjoint, two- and three-dimensional kernels before
 the access, and counts instead of faulting. The edge-size parity tests (lattices of 3 to 4099 nodes on
 every tile shape and depth, ragged periodic and bounce-back batches, paired FP32 lanes at walls and
 joints, the vector and per-node memory paths, the persistent and graph modes with their bounded waits,
-the linear variant, the double-float kernels, the adjoint at every depth, the two-dimensional kernel on
-ragged and tiny lattices) run again in a child process on that build, and every one must leave the
+the linear variant, the double-float kernels, the adjoint at every depth, the two- and three-dimensional
+kernels on ragged and tiny lattices and every configuration of the latter) run again in a child process on that build, and every one must leave the
 record empty."""
 import os
 import subprocess
@@ -23,6 +23,7 @@ SELECTION = [
     ("tests/test_gpu_adjoint.py", "dual_numbers or depths_agree or double_float or fp32_close"),
     ("tests/test_gpu_phys.py", "per_lattice"),
     ("tests/test_gpu_2d.py", "fp64_populations or fp32_matches or one_dimensional or source_off"),
+    ("tests/test_gpu_3d.py", "fp64_populations or configurations_agree or fp32_matches or one_dimensional"),
 ]
 
 
