@@ -745,7 +745,7 @@ def run_2d(args, lbm, torch, side: int, hbm_peak: float):
 
 # Algorithmic bytes of one node update of the three-dimensional scheme: 26 populations read and 26
 # written.
-D3_BYTES_PER_NODE = {"f32": 26 * 2 * 4, "f64": 26 * 2 * 8}
+D3_BYTES_PER_NODE = {"f32": 26 * 2 * 4, "f64": 26 * 2 * 8, "f64df": 26 * 2 * 8}
 # DRAM bytes per node per launch, read + write, from one ncu capture of step3d_kernel (none yet).
 D3_TRAFFIC_BYTES_PER_NODE = {}
 
@@ -762,9 +762,15 @@ def run_3d(args, lbm, torch, side: int, hbm_peak: float):
     N = side ** 3
     out = {"lattice": f"{side} x {side} x {side} periodic",
            "workload": "seeded smooth waves, amplitude 0.05, s_e = 1.2, beta = 9"}
-    for prec in args.precisions.split(","):
-        steps = args.d3_steps_f64 if prec == "f64" else args.d3_steps_f32
+    precs = args.precisions.split(",")
+    if "f64" in precs:
+        precs.append("f64df")  # FP64 planes, double-float arithmetic: FP64 accuracy on the FP32 pipes
+    for prec in precs:
+        steps = {"f64": args.d3_steps_f64, "f64df": args.d3_steps_f64df}.get(prec, args.d3_steps_f32)
         lat = lbm.Lattice3D(side, side, side, precision=prec, s_e=S_E)
+        if args.d3_config:
+            ty, zc, keep = (int(v) for v in args.d3_config.split(","))
+            lat.set_config(ty=ty, zc=zc, keep=keep)
         lat.set_state(*d)
         ms = time_device(lat, torch, steps, 3, None, 1)
         rho = lat.fields(device=True)[0]
@@ -777,7 +783,7 @@ def run_3d(args, lbm, torch, side: int, hbm_peak: float):
         achieved = N * D3_BYTES_PER_NODE[prec] / (launch_ms * 1e-3) / 1e9
         tb = D3_TRAFFIC_BYTES_PER_NODE.get(prec)
         out[prec] = {"value": glups, "unit": UNIT, "steps": steps, "steps_per_launch": 1, "launch_ms": launch_ms,
-                     "finite": finite, "tile_rows": cfg[0], "keep": cfg[2],
+                     "finite": finite, "tile_rows": cfg[0], "planes_per_cta": cfg[1] or "auto", "keep": cfg[2],
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                                   "frac": achieved / hbm_peak, "traffic": None if tb is None else tb * N,
                                   "algorithmic_bytes_per_launch": N * D3_BYTES_PER_NODE[prec]}}
@@ -1102,6 +1108,8 @@ def main():
     ap.add_argument("--d3-side", type=int, default=256)
     ap.add_argument("--d3-steps-f32", type=int, default=100)
     ap.add_argument("--d3-steps-f64", type=int, default=10)
+    ap.add_argument("--d3-steps-f64df", type=int, default=20)
+    ap.add_argument("--d3-config", default="", help="ty,zc,keep of the 3-D kernel (0 / -1: default)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -484,8 +484,8 @@ int lbm2d_fields(lbm2d_ctx *ctx, double *rho, double *ux, double *uy, double *s)
  *  - Production added to zeta after relaxation: dt [rho nu (2 D:D + (div u)^2) / (3T)
  *    + kappa |grad T|^2 / T^2], nu = sigma_e lambda dx, kappa = rho nu c_p / Pr, centred
  *    differences of u and T at time t; then streaming f_i(x + c_i dx) = f_i*(x).
- * Storage: 26 planes of nx * ny * nz values (x fastest, then y, then z), LBM_F64 or LBM_F32_SHIFTED
- * (populations less those of the rest state rho0, u = 0, s0, in units of rho0). Same status codes
+ * Storage: 26 planes of nx * ny * nz values (x fastest, then y, then z), LBM_F64 / LBM_F64_DF or
+ * LBM_F32_SHIFTED (populations less those of the rest state rho0, u = 0, s0, in units of rho0). Same status codes
  * and pointer conventions as the other schemes: arrays may be host or device memory. */
 typedef struct {
   double gamma;   /* > 1 */
@@ -509,7 +509,8 @@ typedef struct {
 typedef struct lbm3d_ctx lbm3d_ctx;
 
 /* nx, ny, nz >= 3 nodes (nx up to 2^30, ny up to 4 * 65535, nx ny nz up to 2^33), precision
- * LBM_F64 or LBM_F32_SHIFTED. LBM_ERR_INVALID_ARG for another precision, a size out of range, a rate
+ * LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (FP64 planes, the node update in double-float on the FP32
+ * pipes, as for the other schemes). LBM_ERR_INVALID_ARG for another precision, a size out of range, a rate
  * outside (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 26-plane state buffers cannot be
  * had. */
 int lbm3d_create(lbm3d_ctx **out, int64_t nx, int64_t ny, int64_t nz, const lbm3d_params *params,
@@ -531,11 +532,12 @@ int lbm3d_get_populations(lbm3d_ctx *ctx, double *f);
 /* The fields rho, ux, uy, uz, s (float64 [nz][ny][nx], host or device, any NULL). */
 int lbm3d_fields(lbm3d_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *s);
 /* Kernel configuration: tile rows ty in {4, 8}, or 16 for FP32 (tiles of 32 x ty columns); the number
- * of planes each CTA marches through along z (zc >= 1, capped at nz); keep = 1 holds a plane's
- * populations in registers across the kernel's barrier, 0 reads them again after it (fewer
- * registers, more CTAs per SM). 0 keeps the current ty or zc, -1 the current keep. Defaults: FP32
- * 8 rows, FP64 4 rows, keep 0, zc from the lattice so that the grid fills the GPU about four times.
- * Every configuration gives the same results bit for bit. */
+ * of planes each CTA marches through along z (zc >= 1, capped at nz); keep, where a thread holds its
+ * populations of plane z across the kernel's barrier: 1 in registers, 2 in a shared buffer of its own
+ * (FP32 with ty 4 only), 0 nowhere (it reads them again after the barrier). 0 keeps the current ty or
+ * zc, -1 the current keep. Defaults: 4 rows; keep 2 for FP32 on 4 rows, else 0; zc from the lattice
+ * so that the grid fills the GPU about eight times. Every configuration gives the same results bit
+ * for bit. */
 int lbm3d_set_config(lbm3d_ctx *ctx, int32_t ty, int32_t zc, int32_t keep);
 int lbm3d_get_config(const lbm3d_ctx *ctx, int32_t *ty, int32_t *zc, int32_t *keep);
 

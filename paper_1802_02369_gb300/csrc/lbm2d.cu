@@ -24,6 +24,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
+#include "lbm_dfn.cuh"
 #include "lbm_internal.cuh"
 
 namespace {
@@ -63,33 +64,21 @@ __host__ __device__ P2T<R> lanes(const P2& p) {
 __device__ __forceinline__ float rcp2d(float x) { return 1.0f / x; }
 __device__ __forceinline__ double rcp2d(double x) { return lbm::m_rcp(x); }
 
-// Double-float numbers for LBM_F64_DF: FP64 storage, the node update in double-float on the FP32 pipes
-// (the operations of lbm_df_core.cuh, about 48 significant bits), behind the operators the update is
-// written with. Construction from a double splits it into the nearest float and the remainder.
-struct dfn {
-  lbm::df v;
-  dfn() = default;
-  __host__ __device__ dfn(double x) : v(lbm::df_from_double_host(x)) {}
-  __device__ explicit dfn(lbm::df x) : v(x) {}
-};
-__device__ __forceinline__ dfn operator+(dfn a, dfn b) { return dfn(lbm::ad(a.v, b.v)); }
-__device__ __forceinline__ dfn operator-(dfn a, dfn b) { return dfn(lbm::sb(a.v, b.v)); }
-__device__ __forceinline__ dfn operator-(dfn a) { return dfn(lbm::df{-a.v.hi, -a.v.lo}); }
-__device__ __forceinline__ dfn operator*(dfn a, dfn b) { return dfn(lbm::ml(a.v, b.v)); }
-__device__ __forceinline__ dfn operator/(dfn a, dfn b) { return dfn(lbm::ml(a.v, lbm::m_rcp(b.v))); }
-__device__ __forceinline__ dfn rcp2d(dfn x) { return dfn(lbm::m_rcp(x.v)); }
+// Double-float numbers for LBM_F64_DF (lbm_dfn.cuh).
+using lbm::dfn;
+__device__ __forceinline__ dfn rcp2d(dfn x) { return lbm::dfn_rcp(x); }
 
 __device__ __forceinline__ float lg2d(float x) { return lbm::m_log1p(x); }
 __device__ __forceinline__ double lg2d(double x) { return lbm::m_log1p(x); }
-__device__ __forceinline__ dfn lg2d(dfn x) { return dfn(lbm::m_log1p(x.v)); }
+__device__ __forceinline__ dfn lg2d(dfn x) { return lbm::dfn_log1p(x); }
 __device__ __forceinline__ float ex2d(float x) { return lbm::m_expm1(x); }
 __device__ __forceinline__ double ex2d(double x) { return lbm::m_expm1(x); }
-__device__ __forceinline__ dfn ex2d(dfn x) { return dfn(lbm::m_expm1(x.v)); }
+__device__ __forceinline__ dfn ex2d(dfn x) { return lbm::dfn_expm1(x); }
 
 // Values as stored (FP32 or FP64 planes).
 __device__ __forceinline__ float stored(float x) { return x; }
 __device__ __forceinline__ double stored(double x) { return x; }
-__device__ __forceinline__ double stored(dfn x) { return lbm::to_double(x.v); }
+__device__ __forceinline__ double stored(dfn x) { return lbm::dfn_store(x); }
 
 // Conserved deviations of shifted populations.
 template <typename R>

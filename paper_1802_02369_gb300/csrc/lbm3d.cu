@@ -38,6 +38,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
+#include "lbm_dfn.cuh"
 #include "lbm_internal.cuh"
 
 namespace {
@@ -90,6 +91,15 @@ __device__ __forceinline__ float lg3(float x) { return lbm::m_log1p(x); }
 __device__ __forceinline__ double lg3(double x) { return lbm::m_log1p(x); }
 __device__ __forceinline__ float ex3(float x) { return lbm::m_expm1(x); }
 __device__ __forceinline__ double ex3(double x) { return lbm::m_expm1(x); }
+// LBM_F64_DF: FP64 planes, the node update in double-float (lbm_dfn.cuh).
+using lbm::dfn;
+__device__ __forceinline__ dfn rcp3(dfn x) { return lbm::dfn_rcp(x); }
+__device__ __forceinline__ dfn lg3(dfn x) { return lbm::dfn_log1p(x); }
+__device__ __forceinline__ dfn ex3(dfn x) { return lbm::dfn_expm1(x); }
+// Values as stored (FP32 or FP64 planes).
+__device__ __forceinline__ float st3(float x) { return x; }
+__device__ __forceinline__ double st3(double x) { return x; }
+__device__ __forceinline__ double st3(dfn x) { return lbm::dfn_store(x); }
 
 // Conserved deviations of shifted populations.
 template <typename R>
@@ -316,16 +326,20 @@ __device__ __forceinline__ void collide3(R (&f)[kQ], const P3T<R>& p, const R (&
 // One time step of the columns of a 32 x TY tile over the planes [z_b, z_b + zc). su[slot][field][n]
 // holds ux, uy, uz, T' of a plane for the tile and a one-node ring around it (n = (ty + 1)(TX + 2)
 // + tx + 1 for thread (tx, ty)); plane z_b - 1 + k goes to slot k mod 4.
-// KEEP holds the populations of plane z in registers across the barrier; otherwise the owner reads
-// them again after it (from L1 or L2: the same thread loaded them one plane earlier), which halves the
-// populations in registers and lets two CTAs share an SM.
-template <typename S, typename R, int TY, bool KEEP>
-__global__ void __launch_bounds__(32 * TY, KEEP ? 1 : ((sizeof(R) == 4 ? 512 : 256) / (32 * TY) > 1 ? (sizeof(R) == 4 ? 512 : 256) / (32 * TY) : 1))
+// MODE says where the owner keeps the populations of plane z across the barrier: 1 in registers;
+// 2 in a shared buffer of its own (two planes, by parity: each thread reads back only what it wrote,
+// so no barrier guards it); 0 nowhere: it reads them again from global memory after the barrier (the
+// same thread loaded them one plane earlier; L2 serves most of them). Modes 0 and 2 halve the
+// populations in registers, so that more CTAs share an SM.
+template <typename S, typename R, int TY, int MODE>
+__global__ void __launch_bounds__(32 * TY, MODE == 1 ? 1 : ((sizeof(R) == 4 ? 512 : 256) / (32 * TY) > 1 ? (sizeof(R) == 4 ? 512 : 256) / (32 * TY) : 1))
     step3d_kernel(const S* __restrict__ in, S* __restrict__ out, int nx, int ny, int nz, int zc, long long N,
                   P3T<R> p) {
   constexpr int TX = 32, RX = TX + 2, RY = TY + 2, NR = RX * RY, NT = TX * TY, NH = NR - NT;
   static_assert(NH <= NT, "the ring around the tile needs one thread per node");
   __shared__ R su[4][4][NR];
+  constexpr int NO = MODE == 2 ? NT : 1;
+  __shared__ R sown[MODE == 2 ? 2 : 1][kQ][NO];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const long long x0 = (long long)blockIdx.x * TX, y0 = (long long)blockIdx.y * TY;
   const long long zb = (long long)blockIdx.z * zc;
@@ -381,6 +395,10 @@ __global__ void __launch_bounds__(32 * TY, KEEP ? 1 : ((sizeof(R) == 4 ? 512 : 2
     }
     load(zb * plane + own_xy, fc);
     reduce(fc, 1, n_own);
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) sown[1][i][threadIdx.x] = fc[i];
+    }
     if (n_h >= 0) {
       load(zb * plane + hxy, f);
       reduce(f, 1, n_h);
@@ -392,13 +410,22 @@ __global__ void __launch_bounds__(32 * TY, KEEP ? 1 : ((sizeof(R) == 4 ? 512 : 2
     R fn[kQ];
     load(zp * plane + own_xy, fn);
     reduce(fn, (k + 1) & 3, n_own);
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) sown[(k + 1) & 1][i][threadIdx.x] = fn[i];
+    }
     if (n_h >= 0) {
       R f[kQ];
       load(zp * plane + hxy, f);
       reduce(f, (k + 1) & 3, n_h);
     }
     __syncthreads();
-    if (!KEEP && owner) load(z * plane + own_xy, fc);
+    if constexpr (MODE == 0) {
+      if (owner) load(z * plane + own_xy, fc);
+    } else if constexpr (MODE == 2) {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) fc[i] = sown[k & 1][i][threadIdx.x];
+    }
     // (n - RX and n + RX bound every shared index of the node: n +- 1 lie between them.)
     if (owner && lbm::in_bounds(n_own - RX, NR) && lbm::in_bounds(n_own + RX, NR)) {
       const int sm = (k - 1) & 3, s0 = k & 3, sp = (k + 1) & 3, n = n_own;
@@ -423,10 +450,10 @@ __global__ void __launch_bounds__(32 * TY, KEEP ? 1 : ((sizeof(R) == 4 ? 512 : 2
 #pragma unroll
       for (int i = 0; i < kQ; ++i) {
         const long long g = zs[cz3(i) + 1] + ys[cy3(i) + 1] + xs[cx3(i) + 1] + i * N;
-        if (lbm::in_bounds(g, kQ * N)) out[g] = S(fc[i]);
+        if (lbm::in_bounds(g, kQ * N)) out[g] = st3(fc[i]);
       }
     }
-    if constexpr (KEEP) {
+    if constexpr (MODE == 1) {
 #pragma unroll
       for (int i = 0; i < kQ; ++i) fc[i] = fn[i];
     }
@@ -494,7 +521,7 @@ struct lbm3d_ctx {
   bool has_state = false;
   long long steps_done = 0;
   int ty = 0, zc = 0;  // 0: default
-  bool keep = false;   // hold plane z in registers across the barrier
+  int keep = -1;  // where plane z waits across the barrier (step3d_kernel's MODE); -1: the default
   std::string err;
   long long n() const { return nx * ny * nz; }
   size_t elem() const { return precision == LBM_F32_SHIFTED ? sizeof(float) : sizeof(double); }
@@ -564,19 +591,24 @@ int derive3(const lbm3d_params* in, P3& p) {
   return LBM_OK;
 }
 
-int default_ty(const lbm3d_ctx* c) { return c->precision == LBM_F32_SHIFTED ? 8 : 4; }
+int default_ty(const lbm3d_ctx*) { return 4; }
+// The shared-buffer variant for FP32 on 4-row tiles (measured fastest there), else the re-read one.
+int default_keep(const lbm3d_ctx* c) {
+  return c->precision == LBM_F32_SHIFTED && (c->ty > 0 ? c->ty : default_ty(c)) == 4 ? 2 : 0;
+}
 
-template <typename S, int TY, bool KEEP>
+template <typename S, typename R, int TY, int MODE>
 cudaError_t launch3(lbm3d_ctx* c) {
   const unsigned gx = (unsigned)((c->nx + 31) / 32), gy = (unsigned)((c->ny + TY - 1) / TY);
   int zc = c->zc;
   if (zc <= 0) {
-    // About four CTAs per resident slot: the planes per CTA follow from the lattice.
+    // About eight CTAs per resident slot (measured at 256^3: 24 planes per CTA 18.3 GLUPS, 52 planes
+    // 17.3): the planes per CTA follow from the lattice.
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step3d_kernel<S, S, TY, KEEP>, 32 * TY, 0);
-    const long long target = 4LL * (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step3d_kernel<S, R, TY, MODE>, 32 * TY, 0);
+    const long long target = 8LL * (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     long long chunks = (target + (long long)gx * gy - 1) / ((long long)gx * gy);
     if (chunks < 1) chunks = 1;
     if (chunks > c->nz) chunks = c->nz;
@@ -585,25 +617,36 @@ cudaError_t launch3(lbm3d_ctx* c) {
   if (zc > c->nz) zc = (int)c->nz;
   const unsigned gz = (unsigned)((c->nz + zc - 1) / zc);
   if (gz > 65535u) return cudaErrorInvalidConfiguration;
-  step3d_kernel<S, S, TY, KEEP><<<dim3(gx, gy, gz), 32 * TY, 0, c->stream>>>(
+  step3d_kernel<S, R, TY, MODE><<<dim3(gx, gy, gz), 32 * TY, 0, c->stream>>>(
       (const S*)c->state[c->cur], (S*)c->state[1 - c->cur], (int)c->nx, (int)c->ny, (int)c->nz, zc, c->n(),
-      lanes3<S>(c->p));
+      lanes3<R>(c->p));
   return cudaGetLastError();
 }
 
-template <bool KEEP>
+template <int MODE>
 cudaError_t launch_step3k(lbm3d_ctx* c) {
   const int ty = c->ty > 0 ? c->ty : default_ty(c);
-  if (c->precision == LBM_F32_SHIFTED) {
-    if (ty == 4) return launch3<float, 4, KEEP>(c);
-    if (ty == 16) return launch3<float, 16, KEEP>(c);
-    return launch3<float, 8, KEEP>(c);
+  if constexpr (MODE == 2) {
+    // FP32 4-row tiles only (the shared buffer of larger tiles passes the 48 KB of static shared
+    // memory); lbm3d_set_config refuses the rest.
+    if (c->precision != LBM_F32_SHIFTED || ty != 4) return cudaErrorInvalidConfiguration;
+    return launch3<float, float, 4, 2>(c);
+  } else {
+    if (c->precision == LBM_F32_SHIFTED) {
+      if (ty == 4) return launch3<float, float, 4, MODE>(c);
+      if (ty == 16) return launch3<float, float, 16, MODE>(c);
+      return launch3<float, float, 8, MODE>(c);
+    }
+    if (c->precision == LBM_F64_DF) return ty == 8 ? launch3<double, dfn, 8, MODE>(c) : launch3<double, dfn, 4, MODE>(c);
+    if (ty == 8) return launch3<double, double, 8, MODE>(c);
+    return launch3<double, double, 4, MODE>(c);
   }
-  if (ty == 8) return launch3<double, 8, KEEP>(c);
-  return launch3<double, 4, KEEP>(c);
 }
 
-cudaError_t launch_step3(lbm3d_ctx* c) { return c->keep ? launch_step3k<true>(c) : launch_step3k<false>(c); }
+cudaError_t launch_step3(lbm3d_ctx* c) {
+  const int mode = c->keep >= 0 ? c->keep : default_keep(c);
+  return mode == 1 ? launch_step3k<1>(c) : mode == 2 ? launch_step3k<2>(c) : launch_step3k<0>(c);
+}
 
 int ensure_stage3(lbm3d_ctx* c) {
   if (c->d_stage) return LBM_OK;
@@ -635,7 +678,7 @@ int lbm3d_create(lbm3d_ctx** out, int64_t nx, int64_t ny, int64_t nz, const lbm3
   if (nx < 3 || ny < 3 || nz < 3 || nx > (1LL << 30) || ny > 4LL * 65535 || nz > (1LL << 30) ||
       nx * ny > (1LL << 33) || nx * ny * nz > (1LL << 33))
     return LBM_ERR_INVALID_ARG;
-  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED) return LBM_ERR_INVALID_ARG;
+  if (precision != LBM_F64 && precision != LBM_F32_SHIFTED && precision != LBM_F64_DF) return LBM_ERR_INVALID_ARG;
   P3 p{};
   if (int rc = derive3(params, p)) return rc;
   lbm3d_ctx* c = new lbm3d_ctx();
@@ -679,14 +722,15 @@ int lbm3d_rates(const lbm3d_ctx* c, double* rates) {
 
 int lbm3d_set_config(lbm3d_ctx* c, int32_t ty, int32_t zc, int32_t keep) {
   if (!c) return LBM_ERR_INVALID_ARG;
-  if (keep < -1 || keep > 1) return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: keep must be -1, 0 or 1");
-  const bool f32 = c->precision == LBM_F32_SHIFTED;
-  if (ty != 0 && ty != 4 && ty != 8 && !(f32 && ty == 16))
-    return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: ty must be 4, 8 (or 16 for FP32)");
+  if (keep < -1 || keep > 2) return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: keep must be -1, 0, 1 or 2");
+  if (keep == 2 && (c->precision != LBM_F32_SHIFTED || (ty ? ty : (c->ty > 0 ? c->ty : default_ty(c))) != 4))
+    return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: keep 2 (shared buffer) takes FP32 and ty 4");
+  if (keep == -1 && c->keep == 2 && ty && ty != 4)
+    return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: keep 2 (shared buffer) takes ty 4");
   if (zc < 0) return fail3(c, LBM_ERR_INVALID_ARG, "lbm3d_set_config: zc < 0");
   if (ty) c->ty = ty;
   if (zc) c->zc = zc;
-  if (keep >= 0) c->keep = keep == 1;
+  if (keep >= 0) c->keep = keep;
   return LBM_OK;
 }
 
@@ -694,7 +738,7 @@ int lbm3d_get_config(const lbm3d_ctx* c, int32_t* ty, int32_t* zc, int32_t* keep
   if (!c) return LBM_ERR_INVALID_ARG;
   if (ty) *ty = c->ty > 0 ? c->ty : default_ty(c);
   if (zc) *zc = c->zc;
-  if (keep) *keep = c->keep ? 1 : 0;
+  if (keep) *keep = c->keep >= 0 ? c->keep : default_keep(c);
   return LBM_OK;
 }
 

@@ -754,7 +754,7 @@ class Lattice2D:
 
 class Lattice3D:
     """Three-dimensional coupled D3Q19-D3Q7 scheme (lbm3d_* of the C-ABI) on a periodic nx x ny x nz
-    lattice; precision "f64" or "f32". Fields are [nz, ny, nx] arrays (x fastest); populations
+    lattice; precision "f64", "f64df" or "f32". Fields are [nz, ny, nx] arrays (x fastest); populations
     [nz, ny, nx, 26] in the order (f0..f18, g0..g6). Keyword parameters are the lbm3d_params fields
     (gamma, Pr, cp, rho0, p0, s0, lam, dx, beta, s_e, s_psi, s_eps, s_q, s_h, source_on); the defaults
     are the section 9 values with beta = 9, s_q = 1.5, s_h = 1.2, s_eps = 1."""

@@ -73,7 +73,7 @@ def test_invalid_arguments_are_rejected_without_gpu(lib_path):
     assert lib.lbm2d_create(ctypes.byref(ctx), 16, 4 * 65535 + 1, ctypes.byref(p2), 0, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm2d_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm2d_steps_done(None) == -1
-    # The three-dimensional scheme: same parameter checks, sizes, and FP64 / FP32 only.
+    # The three-dimensional scheme: same parameter checks, sizes and precisions.
     for change in (dict(s_e=2.0), dict(gamma=1.0), dict(lam=0.0), dict(s_h=2.5), dict(rho0=-1.0), dict(Pr=0.0),
                    dict(s_eps=-0.0 + 2.0), dict(cp=0.0)):
         p3 = lbm.lbm3d_params(**{**ok2, **change})
@@ -81,7 +81,7 @@ def test_invalid_arguments_are_rejected_without_gpu(lib_path):
     p3 = lbm.lbm3d_params(**ok2)
     for dims in ((2, 16, 16), (16, 2, 16), (16, 16, 2), (16, 4 * 65535 + 1, 16), (1 << 20, 1 << 10, 1 << 4)):
         assert lib.lbm3d_create(ctypes.byref(ctx), *dims, ctypes.byref(p3), 0, None) == lbm.LBM_ERR_INVALID_ARG, dims
-    for precision in (2, 3, -1):
+    for precision in (3, -1):
         assert lib.lbm3d_create(ctypes.byref(ctx), 16, 16, 16, ctypes.byref(p3), precision, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm3d_create(None, 16, 16, 16, ctypes.byref(p3), 0, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm3d_create(ctypes.byref(ctx), 16, 16, 16, None, 0, None) == lbm.LBM_ERR_INVALID_ARG

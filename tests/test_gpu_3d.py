@@ -1,8 +1,8 @@
 """Parity of the three-dimensional D3Q19-D3Q7 kernel (through the C-ABI) with the FP64 CPU oracle.
 
-Populations are compared element by element in units of rho0: FP64 within 1e-12 (absolute; the
-populations are of order 0.01 to 0.5), FP32 within 1e-5 of the fields' scales (rho0, lambda, c_p) on
-rho, u, s and within 1e-5 on the populations."""
+Populations are compared element by element in units of rho0: FP64 and double-float within 1e-12
+(absolute; the populations are of order 0.01 to 0.5), FP32 within 1e-5 of the fields' scales (rho0,
+lambda, c_p) on rho, u, s and within 1e-5 on the populations."""
 import numpy as np
 import pytest
 
@@ -49,24 +49,29 @@ def run_both(D, lbm, nx, ny, nz, steps, precision, kw, s_e=1.2, beta=9.0, seed=1
     return ph, ref, pops, got_fields
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64df"])
 @pytest.mark.parametrize("kw", PHYS)
 @pytest.mark.parametrize("shape", [(37, 11, 7), (3, 3, 3), (5, 19, 4), (33, 4, 9)])
-def test_fp64_populations_match_the_oracle(D, lbm, kw, shape):
+def test_fp64_populations_match_the_oracle(D, lbm, kw, shape, precision):
     """Ragged tile edges (37 x 11 on 32 x 4 tiles), lattices smaller than the tile and its ring (the
-    periodic wrap taken several times along every axis), non-default physics."""
-    _, ref, pops, _ = run_both(D, lbm, *shape, 20, "f64", kw)
+    periodic wrap taken several times along every axis), non-default physics; FP64 and double-float
+    arithmetic."""
+    _, ref, pops, _ = run_both(D, lbm, *shape, 20, precision, kw)
     assert np.abs(pops - ref).max() <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f64df", "f32"])
 def test_kernel_configurations_agree_bit_for_bit(D, lbm, precision):
-    """Tile rows, planes per CTA (one plane, a ragged last chunk, all planes) and the register or
-    re-read variant change the schedule only: the populations are identical."""
+    """Tile rows, planes per CTA (one plane, a ragged last chunk, all planes) and where a plane's
+    populations wait across the barrier (re-read, registers, shared buffer) change the schedule only:
+    the populations are identical."""
     fields = W.waves_3d(40, 21, 13, 3, amp=0.05)
     outs = []
-    configs = [dict(ty=4, zc=1, keep=0), dict(ty=8, zc=5, keep=1), dict(ty=4, zc=13, keep=1), dict(ty=8, zc=4, keep=0)]
+    configs = [dict(ty=4, zc=1, keep=0), dict(ty=8, zc=5, keep=1), dict(ty=4, zc=13, keep=1), dict(ty=8, zc=4, keep=0),
+               dict(ty=4, zc=6, keep=0)]
     if precision == "f32":
-        configs.append(dict(ty=16, zc=3, keep=0))
+        configs += [dict(ty=16, zc=3, keep=0), dict(ty=16, zc=2, keep=1), dict(ty=4, zc=1, keep=2),
+                    dict(ty=4, zc=5, keep=2), dict(ty=4, zc=13, keep=2)]
     for cfg in configs:
         lat = lbm.Lattice3D(40, 21, 13, precision=precision, s_e=1.3)
         lat.set_config(**cfg)
@@ -124,14 +129,14 @@ def test_source_off_and_rates(D, lbm):
     lat.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f64df", 1e-12), ("f32", 1e-5)])
 def test_long_horizon(D, lbm, precision, tol):
     """300 steps on a 24 x 20 x 16 lattice: the errors stay within the same bounds."""
     _, ref, pops, _ = run_both(D, lbm, 24, 20, 16, 300, precision, {}, seed=13)
     assert np.abs(pops - ref).max() <= tol
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f64df", "f32"])
 def test_full_size_sampled_windows(D, lbm, precision):
     """A 256 x 256 x 256 lattice after 6 steps, compared on 8 x 8 x 8 windows: the oracle runs each
     window with a halo of 2 nodes per step (the dependency radius of a step: streaming plus the centred
