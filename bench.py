@@ -746,8 +746,10 @@ def run_2d(args, lbm, torch, side: int, hbm_peak: float):
 # Algorithmic bytes of one node update of the three-dimensional scheme: 26 populations read and 26
 # written.
 D3_BYTES_PER_NODE = {"f32": 26 * 2 * 4, "f64": 26 * 2 * 8, "f64df": 26 * 2 * 8}
-# DRAM bytes per node per launch, read + write, from one ncu capture of step3d_kernel (none yet).
-D3_TRAFFIC_BYTES_PER_NODE = {}
+# DRAM bytes per node per launch, read + write, from one ncu capture of step3d_kernel each: FP32
+# (shared-buffer variant) on a 128^3 lattice, FP64 on 96^3 (both states above L2), scaled by the nodes.
+D3_TRAFFIC_BYTES_PER_NODE = {"f32": (222.251008e6 + 177.752576e6) / 128 ** 3,
+                             "f64": (188.406528e6 + 146.721792e6) / 96 ** 3}
 
 
 def run_3d(args, lbm, torch, side: int, hbm_peak: float):
