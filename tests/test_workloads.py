@@ -40,3 +40,22 @@ def test_ragged_batch_deterministic_and_filtered():
     assert f.s_e.min() >= 1.0 and f.s_e.max() <= 1.9
     g = W.ragged_batch(64, 7, 0.25 / 1.4, n_min=33, n_max=300, entropy_range=(-0.15, 0.0), stable_flow=True)
     assert np.array_equal(f.rho, g.rho)
+
+
+def test_waves_windows_regenerate_the_full_lattice():
+    """A window generated alone with ``period`` equals the same window of the full periodic lattice,
+    including windows that wrap past the edges (the full-size parity tests rely on this), in two and
+    three dimensions; the entropy stays within the three-dimensional scheme's stable range."""
+    full = W.waves_2d(40, 24, 23, amp=0.05)
+    win = W.waves_2d(9, 7, 23, amp=0.05, x0=35, y0=-3, period=(40, 24))
+    ys, xs = (np.arange(-3, 4) % 24)[:, None], (np.arange(35, 44) % 40)[None, :]
+    for a, b in zip(full, win):
+        assert np.array_equal(a[ys, xs], b)
+    full = W.waves_3d(20, 12, 10, 23, amp=0.05)
+    win = W.waves_3d(6, 5, 4, 23, amp=0.05, x0=17, y0=-2, z0=8, period=(20, 12, 10))
+    zs = (np.arange(8, 12) % 10)[:, None, None]
+    ys = (np.arange(-2, 3) % 12)[None, :, None]
+    xs = (np.arange(17, 23) % 20)[None, None, :]
+    for a, b in zip(full, win):
+        assert np.array_equal(a[zs, ys, xs], b)
+    assert np.abs(full[4]).max() <= 0.05
