@@ -532,7 +532,8 @@ int lbm3d_get_populations(lbm3d_ctx *ctx, double *f);
 /* The fields rho, ux, uy, uz, s (float64 [nz][ny][nx], host or device, any NULL). */
 int lbm3d_fields(lbm3d_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *s);
 /* Kernel configuration: tile rows ty in {4, 8}, or 16 for FP32 (tiles of 32 x ty columns); the number
- * of planes each CTA marches through along z (zc >= 1, capped at nz); keep, where a thread holds its
+ * of planes each CTA marches through along z (zc >= 1, capped at nz and raised to nz / 65535 where
+ * the grid needs it); keep, where a thread holds its
  * populations of plane z across the kernel's barrier: 1 in registers, 2 in a shared buffer of its own
  * (FP32 with ty 4 only), 0 nowhere (it reads them again after the barrier). 0 keeps the current ty or
  * zc, -1 the current keep. Defaults: 4 rows; keep 2 for FP32 on 4 rows, else 0; zc from the lattice

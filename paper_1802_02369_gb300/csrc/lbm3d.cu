@@ -96,10 +96,30 @@ using lbm::dfn;
 __device__ __forceinline__ dfn rcp3(dfn x) { return lbm::dfn_rcp(x); }
 __device__ __forceinline__ dfn lg3(dfn x) { return lbm::dfn_log1p(x); }
 __device__ __forceinline__ dfn ex3(dfn x) { return lbm::dfn_expm1(x); }
-// Values as stored (FP32 or FP64 planes).
+// Storage. FP32 and FP64 planes hold floats and doubles; the double-float planes hold each population
+// as its (hi, lo) FP32 pair (8 bytes, as a double), so that the step loads and stores them with no
+// conversion on the FP64 pipe (measured: with FP64 planes the conversions at the 26 loads, the
+// re-read and the ring, and the 26 stores kept that pipe 63 % busy and bounded the kernel).
 __device__ __forceinline__ float st3(float x) { return x; }
 __device__ __forceinline__ double st3(double x) { return x; }
-__device__ __forceinline__ double st3(dfn x) { return lbm::dfn_store(x); }
+__device__ __forceinline__ float2 st3(dfn x) { return make_float2(x.v.hi, x.v.lo); }
+template <typename R>
+__device__ __forceinline__ R ld3(float x) { return R(x); }
+template <typename R>
+__device__ __forceinline__ R ld3(double x) { return R(x); }
+template <typename R>
+__device__ __forceinline__ R ld3(float2 x) { return R(lbm::df{x.x, x.y}); }
+// FP64 values of stored populations and the stored form of FP64 values (initialisation, read-out).
+__host__ __device__ __forceinline__ double from_store(float x) { return (double)x; }
+__host__ __device__ __forceinline__ double from_store(double x) { return x; }
+__host__ __device__ __forceinline__ double from_store(float2 x) { return (double)x.x + (double)x.y; }
+template <typename S>
+__host__ __device__ __forceinline__ S to_store(double x) { return S(x); }
+template <>
+__host__ __device__ __forceinline__ float2 to_store<float2>(double x) {
+  const lbm::df d = lbm::df_from_double_host(x);
+  return make_float2(d.hi, d.lo);
+}
 
 // Conserved deviations of shifted populations.
 template <typename R>
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__(32 * TY, MODE == 1 ? 1 : ((sizeof(R) == 4 ? 51
   const long long plane = (long long)nx * ny;
   auto load = [&](long long g, R (&f)[kQ]) {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) f[i] = lbm::in_bounds(g + i * N, kQ * N) ? R(in[g + i * N]) : R(0);
+    for (int i = 0; i < kQ; ++i) f[i] = lbm::in_bounds(g + i * N, kQ * N) ? ld3<R>(in[g + i * N]) : R(0);
   };
   auto reduce = [&](const R (&f)[kQ], int slot, int n) {
     if (!lbm::in_bounds(n, NR)) return;
@@ -479,7 +499,7 @@ __global__ void init3d_kernel(const double* __restrict__ rho, const double* __re
   equilibria3(c, t, q, eq);
   populations3(c, eq, f);
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) st[k * n + i] = S(f[k]);
+  for (int k = 0; k < kQ; ++k) st[k * n + i] = to_store<S>(f[k]);
 }
 
 // Populations, node-major and unshifted, in FP64.
@@ -488,7 +508,7 @@ __global__ void pops3d_kernel(const S* __restrict__ st, double* __restrict__ out
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) out[kQ * i + k] = (double)st[k * n + i] + p.w[k];
+  for (int k = 0; k < kQ; ++k) out[kQ * i + k] = from_store(st[k * n + i]) + p.w[k];
 }
 
 template <typename S>
@@ -498,7 +518,7 @@ __global__ void fields3d_kernel(const S* __restrict__ st, long long n, P3 p, dou
   if (i >= n) return;
   double f[kQ];
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) f[k] = (double)st[k * n + i];
+  for (int k = 0; k < kQ; ++k) f[k] = from_store(st[k * n + i]);
   const Cons3<double> c = conserved3(f);
   const double r1 = 1.0 + c.r;
   if (rho) rho[i] = p.rho0 * r1;
@@ -615,8 +635,10 @@ cudaError_t launch3(lbm3d_ctx* c) {
     zc = (int)((c->nz + chunks - 1) / chunks);
   }
   if (zc > c->nz) zc = (int)c->nz;
+  // At most 65535 CTAs along z: a taller lattice takes more planes per CTA than asked.
+  const long long zc_min = (c->nz + 65534) / 65535;
+  if (zc < zc_min) zc = (int)zc_min;
   const unsigned gz = (unsigned)((c->nz + zc - 1) / zc);
-  if (gz > 65535u) return cudaErrorInvalidConfiguration;
   step3d_kernel<S, R, TY, MODE><<<dim3(gx, gy, gz), 32 * TY, 0, c->stream>>>(
       (const S*)c->state[c->cur], (S*)c->state[1 - c->cur], (int)c->nx, (int)c->ny, (int)c->nz, zc, c->n(),
       lanes3<R>(c->p));
@@ -637,7 +659,7 @@ cudaError_t launch_step3k(lbm3d_ctx* c) {
       if (ty == 16) return launch3<float, float, 16, MODE>(c);
       return launch3<float, float, 8, MODE>(c);
     }
-    if (c->precision == LBM_F64_DF) return ty == 8 ? launch3<double, dfn, 8, MODE>(c) : launch3<double, dfn, 4, MODE>(c);
+    if (c->precision == LBM_F64_DF) return ty == 8 ? launch3<float2, dfn, 8, MODE>(c) : launch3<float2, dfn, 4, MODE>(c);
     if (ty == 8) return launch3<double, double, 8, MODE>(c);
     return launch3<double, double, 4, MODE>(c);
   }
@@ -760,7 +782,10 @@ int lbm3d_set_state(lbm3d_ctx* c, const double* rho, const double* ux, const dou
       d[k] = c->d_stage + k * n;
     }
   }
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    init3d_kernel<float2><<<blocks3(n, 256), 256, 0, c->stream>>>(d[0], d[1], d[2], d[3], d[4],
+                                                                   (float2*)c->state[c->cur], n, c->p);
+  else if (c->precision != LBM_F32_SHIFTED)
     init3d_kernel<double><<<blocks3(n, 256), 256, 0, c->stream>>>(d[0], d[1], d[2], d[3], d[4],
                                                                    (double*)c->state[c->cur], n, c->p);
   else
@@ -796,7 +821,9 @@ int lbm3d_get_populations(lbm3d_ctx* c, double* f) {
   if (host)
     if (int rc = ensure_stage3(c)) return rc;
   double* d = host ? c->d_stage : f;
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    pops3d_kernel<float2><<<blocks3(n, 256), 256, 0, c->stream>>>((const float2*)c->state[c->cur], d, n, c->p);
+  else if (c->precision != LBM_F32_SHIFTED)
     pops3d_kernel<double><<<blocks3(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], d, n, c->p);
   else
     pops3d_kernel<float><<<blocks3(n, 256), 256, 0, c->stream>>>((const float*)c->state[c->cur], d, n, c->p);
@@ -822,7 +849,10 @@ int lbm3d_fields(lbm3d_ctx* c, double* rho, double* ux, double* uy, double* uz, 
     if (int rc = ensure_stage3(c)) return rc;
   double* d[5];
   for (int k = 0; k < 5; ++k) d[k] = outs[k] ? (host[k] ? c->d_stage + k * n : outs[k]) : nullptr;
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    fields3d_kernel<float2><<<blocks3(n, 256), 256, 0, c->stream>>>((const float2*)c->state[c->cur], n, c->p, d[0],
+                                                                      d[1], d[2], d[3], d[4]);
+  else if (c->precision != LBM_F32_SHIFTED)
     fields3d_kernel<double><<<blocks3(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->p, d[0],
                                                                       d[1], d[2], d[3], d[4]);
   else
