@@ -76,9 +76,28 @@ __device__ __forceinline__ double ex2d(double x) { return lbm::m_expm1(x); }
 __device__ __forceinline__ dfn ex2d(dfn x) { return lbm::dfn_expm1(x); }
 
 // Values as stored (FP32 or FP64 planes).
+// The double-float planes hold each population as its (hi, lo) FP32 pair (8 bytes, as a double), so
+// that the step converts nothing on the FP64 pipe at its loads and stores.
 __device__ __forceinline__ float stored(float x) { return x; }
 __device__ __forceinline__ double stored(double x) { return x; }
-__device__ __forceinline__ double stored(dfn x) { return lbm::dfn_store(x); }
+__device__ __forceinline__ float2 stored(dfn x) { return make_float2(x.v.hi, x.v.lo); }
+template <typename R>
+__device__ __forceinline__ R loaded(float x) { return R(x); }
+template <typename R>
+__device__ __forceinline__ R loaded(double x) { return R(x); }
+template <typename R>
+__device__ __forceinline__ R loaded(float2 x) { return R(lbm::df{x.x, x.y}); }
+// FP64 values of stored populations and the stored form of FP64 values (initialisation, read-out).
+__device__ __forceinline__ double from_stored(float x) { return (double)x; }
+__device__ __forceinline__ double from_stored(double x) { return x; }
+__device__ __forceinline__ double from_stored(float2 x) { return (double)x.x + (double)x.y; }
+template <typename S>
+__device__ __forceinline__ S to_stored(double x) { return S(x); }
+template <>
+__device__ __forceinline__ float2 to_stored<float2>(double x) {
+  const lbm::df d = lbm::df_from_double_host(x);
+  return make_float2(d.hi, d.lo);
+}
 
 // Conserved deviations of shifted populations.
 template <typename R>
@@ -192,7 +211,7 @@ __device__ __forceinline__ long long wrap(long long v, long long n) {
 // One time step of a 32 x TY tile: the tile and a halo of 2 nodes are read into shared memory with
 // their velocity and temperature deviation; the tile and a ring of 1 node collide (the production
 // needs the neighbours' u and T'); the tile pulls its populations from the collided neighbours.
-// S is the storage type of the planes, R the arithmetic (float, double, or dfn over double planes).
+// S is the storage type of the planes, R the arithmetic (float, double, or dfn over planes of FP32 pairs).
 template <typename S, typename R, int TY, bool REUSE>
 __global__ void __launch_bounds__(32 * TY) step2d_kernel(const S* __restrict__ in, S* __restrict__ out, int nx, int ny,
                                                          long long plane, P2T<R> p) {
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(32 * TY) step2d_kernel(const S* __restrict__ i
     R f[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      f[i] = lbm::in_bounds(g + i * plane, kQ * plane) ? R(in[g + i * plane]) : R(0);
+      f[i] = lbm::in_bounds(g + i * plane, kQ * plane) ? loaded<R>(in[g + i * plane]) : R(0);
       sf[i][k] = f[i];
     }
     const Cons<R> c = conserved(f);
@@ -302,7 +321,7 @@ __global__ void init2d_kernel(const double* __restrict__ rho, const double* __re
   equilibria(c, t, q, eq);
   populations(c, eq, f);
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) st[k * n + i] = R(f[k]);
+  for (int k = 0; k < kQ; ++k) st[k * n + i] = to_stored<R>(f[k]);
 }
 
 // Populations, node-major and unshifted, in FP64.
@@ -311,7 +330,7 @@ __global__ void pops2d_kernel(const R* __restrict__ st, double* __restrict__ out
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) out[kQ * i + k] = (double)st[k * n + i] + p.w[k];
+  for (int k = 0; k < kQ; ++k) out[kQ * i + k] = from_stored(st[k * n + i]) + p.w[k];
 }
 
 template <typename R>
@@ -321,7 +340,7 @@ __global__ void fields2d_kernel(const R* __restrict__ st, long long n, P2 p, dou
   if (i >= n) return;
   double f[kQ];
 #pragma unroll
-  for (int k = 0; k < kQ; ++k) f[k] = (double)st[k * n + i];
+  for (int k = 0; k < kQ; ++k) f[k] = from_stored(st[k * n + i]);
   const Cons<double> c = conserved(f);
   const double r1 = 1.0 + c.r;
   if (rho) rho[i] = p.rho0 * r1;
@@ -516,7 +535,9 @@ int lbm2d_set_state(lbm2d_ctx* c, const double* rho, const double* ux, const dou
     d = c->d_stage + 2 * n;
     e = c->d_stage + 3 * n;
   }
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    init2d_kernel<float2><<<blocks_for(n, 256), 256, 0, c->stream>>>(a, b, d, e, (float2*)c->state[c->cur], n, c->p);
+  else if (c->precision != LBM_F32_SHIFTED)
     init2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>(a, b, d, e, (double*)c->state[c->cur], n, c->p);
   else
     init2d_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>(a, b, d, e, (float*)c->state[c->cur], n, c->p);
@@ -534,7 +555,7 @@ int lbm2d_step(lbm2d_ctx* c, int64_t nsteps) {
   if (!c->has_state) return fail(c, LBM_ERR_INVALID_ARG, "lbm2d_step: no state set");
   for (int64_t k = 0; k < nsteps; ++k) {
     const cudaError_t e = c->precision == LBM_F32_SHIFTED ? launch_step<float, float>(c)
-                          : c->precision == LBM_F64_DF   ? launch_step<double, dfn>(c)
+                          : c->precision == LBM_F64_DF   ? launch_step<float2, dfn>(c)
                                                          : launch_step<double, double>(c);
     if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("lbm2d step launch: ") + cudaGetErrorString(e));
     c->cur = 1 - c->cur;
@@ -552,7 +573,9 @@ int lbm2d_get_populations(lbm2d_ctx* c, double* f) {
   if (host)
     if (int rc = ensure_stage(c)) return rc;
   double* d = host ? c->d_stage : f;
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    pops2d_kernel<float2><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float2*)c->state[c->cur], d, n, c->p);
+  else if (c->precision != LBM_F32_SHIFTED)
     pops2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], d, n, c->p);
   else
     pops2d_kernel<float><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float*)c->state[c->cur], d, n, c->p);
@@ -578,7 +601,10 @@ int lbm2d_fields(lbm2d_ctx* c, double* rho, double* ux, double* uy, double* s) {
     if (int rc = ensure_stage(c)) return rc;
   double* d[4];
   for (int k = 0; k < 4; ++k) d[k] = outs[k] ? (host[k] ? c->d_stage + k * n : outs[k]) : nullptr;
-  if (c->precision != LBM_F32_SHIFTED)
+  if (c->precision == LBM_F64_DF)
+    fields2d_kernel<float2><<<blocks_for(n, 256), 256, 0, c->stream>>>((const float2*)c->state[c->cur], n, c->p, d[0],
+                                                                         d[1], d[2], d[3]);
+  else if (c->precision != LBM_F32_SHIFTED)
     fields2d_kernel<double><<<blocks_for(n, 256), 256, 0, c->stream>>>((const double*)c->state[c->cur], n, c->p, d[0],
                                                                          d[1], d[2], d[3]);
   else
