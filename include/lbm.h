@@ -436,8 +436,8 @@ typedef struct {
 
 typedef struct lbm2d_ctx lbm2d_ctx;
 
-/* nx, ny >= 3 nodes, precision LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (FP64 planes, the node update in
- * double-float on the FP32 pipes, as for the one-dimensional scheme). LBM_ERR_INVALID_ARG for a rate outside
+/* nx, ny >= 3 nodes, precision LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (planes of 8-byte (hi, lo) FP32 pairs,
+ * the node update in double-float on the FP32 pipes; FP64 accuracy). LBM_ERR_INVALID_ARG for a rate outside
  * (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 14-plane state buffers cannot be had. */
 int lbm2d_create(lbm2d_ctx **out, int64_t nx, int64_t ny, const lbm2d_params *params, int32_t precision,
                  void *stream);
@@ -509,8 +509,8 @@ typedef struct {
 typedef struct lbm3d_ctx lbm3d_ctx;
 
 /* nx, ny, nz >= 3 nodes (nx up to 2^30, ny up to 4 * 65535, nx ny nz up to 2^33), precision
- * LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (FP64 planes, the node update in double-float on the FP32
- * pipes, as for the other schemes). LBM_ERR_INVALID_ARG for another precision, a size out of range, a rate
+ * LBM_F64, LBM_F32_SHIFTED or LBM_F64_DF (planes of 8-byte (hi, lo) FP32 pairs, the node update in
+ * double-float on the FP32 pipes; FP64 accuracy). LBM_ERR_INVALID_ARG for another precision, a size out of range, a rate
  * outside (0, 2) or a non-positive constant; LBM_ERR_OOM if the two 26-plane state buffers cannot be
  * had. */
 int lbm3d_create(lbm3d_ctx **out, int64_t nx, int64_t ny, int64_t nz, const lbm3d_params *params,
