@@ -63,7 +63,9 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
  *   the FP64 tolerance (1e-12 relative after 1000 steps; about 1e-14 per step); initialisation,
  *   moments and diagnostics run in FP64 as for LBM_F64, the adjoint in double-float.
  *   Only LBM_MODE_LAUNCH; kernel configurations: steps_per_launch in {1, 2, 4, 8}, block_threads in
- *   {128, 256, 512}, nodes_per_thread in {1, 2, 4} (2 and 4 on paired FP32 lanes, bitwise equal to 1). */
+ *   {128, 256, 512}, nodes_per_thread in {1, 2, 4} (2 and 4 on paired FP32 lanes, bitwise equal to 1).
+ *   The two- and three-dimensional schemes, one step per launch, store the (hi, lo) pairs themselves
+ *   (8 bytes a population, as FP64) so that their steps convert nothing on the FP64 pipe. */
 enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F64_DF = 2 };
 
 /* Relaxation rates of step (iii). s_e is the free rate (eq. henon-d1q3q3, nu = sigma_e lambda dx).
