@@ -24,12 +24,13 @@
 // 72, 24), so the inverse is the transpose divided by the norms; the D3Q7 inverse is written out.
 //
 // The step kernel. Thread (tx, ty) of a CTA owns the nodes (x0 + tx, y0 + ty, z) of its column. For
-// each plane z it holds the populations of z in registers while those of z + 1 load; the velocity
-// and temperature deviation of plane z + 1 go to a ring of four shared slots, with a one-node ring
-// around the tile (loaded and reduced by the first threads: the production needs the neighbours' u
-// and T'). One barrier a plane: the ring has four slots, so a warp that runs ahead writes the slot of
-// z + 2 while the others still read z - 1, z and z + 1. Then the node of plane z collides and pushes
-// its populations to the neighbours, f_i(x + c_i) = f_i*(x): each population is read once and
+// each plane z it loads the populations of plane z + 1 and reduces them to the velocity and temperature
+// deviation, which go to a ring of four shared slots with a one-node ring around the tile (loaded and
+// reduced by the first threads: the production needs the neighbours' u and T'). One barrier a plane:
+// the ring has four slots, so a warp that runs ahead writes the slot of z + 2 while the others still
+// read z - 1, z and z + 1. Then the node of plane z, whose populations waited across the barrier (in
+// a shared buffer of the thread's own, in registers, or re-read: MODE below), collides and pushes its
+// populations to the neighbours, f_i(x + c_i) = f_i*(x): each population is read once from DRAM and
 // written once per step.
 #include <cmath>
 #include <string>
