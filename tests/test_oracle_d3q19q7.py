@@ -317,3 +317,37 @@ def test_conservation_and_uniform_state():
     one = np.ones((3, 4, 5))
     f = D.init(ph, 1.1 * one, 0.05 * one, -0.03 * one, 0.02 * one, 0.02 * one)
     assert np.abs(D.run(ph, rt, f, 3) - f).max() <= 1e-14
+
+
+def _sound_speed(ph, rt, shape, kvec, N, t1, t2):
+    """Phase speed of a right-going isentropic acoustic wave of wave vector 2 pi kvec / N, from the phase of
+    its density mode between steps t1 and t2."""
+    zz, yy, xx = np.mgrid[0:shape[0], 0:shape[1], 0:shape[2]].astype(float)
+    k = [2 * np.pi * a / N for a in kvec]
+    kk = np.sqrt(sum(a * a for a in k))
+    phase = k[0] * xx + k[1] * yy + k[2] * zz
+    c0 = np.sqrt(ph.gamma * ph.p0 / ph.rho0)
+    A = 1e-5
+    rho = ph.rho0 * (1 + A * np.cos(phase))
+    un = c0 * A * np.cos(phase)
+    f = D.init(ph, rho, *(un * a / kk for a in k), np.zeros_like(rho) + ph.s0)
+    a = D.run(ph, rt, f, t1, NT)
+    b = D.run(ph, rt, a, t2 - t1, NT)
+    ang = lambda f: np.angle(np.sum((D.moments(ph, f)[..., 0] - ph.rho0) * np.exp(-1j * phase)))
+    d = -((ang(b) - ang(a) + np.pi) % (2 * np.pi) - np.pi)
+    return d / kk / (t2 - t1), kk
+
+
+def test_sound_speed_is_isotropic():
+    """Acoustic waves travel at the same speed along an axis, a face diagonal and the body diagonal at
+    (nearly) the same |k| (0.3 %, 1 %), and near c0 = sqrt(gamma p0 / rho0) (the scheme's own offset,
+    the same in the one-dimensional oracle, is 3 % at these wavelengths and s_e = 1.2)."""
+    ph, rt = D.default_phys(source_on=0), D.rates(1.2)
+    c0 = np.sqrt(ph.gamma * ph.p0 / ph.rho0)
+    ax, k_ax = _sound_speed(ph, rt, (3, 3, 45), (1, 0, 0), 45, 10, 30)
+    fd, k_fd = _sound_speed(ph, rt, (3, 64, 64), (1, 1, 0), 64, 10, 30)
+    assert abs(k_fd / k_ax - 1) < 0.01 and abs(fd / ax - 1) <= 0.003
+    assert abs(ax / c0 - 1) <= 0.04
+    ax, k_ax = _sound_speed(ph, rt, (3, 3, 14), (1, 0, 0), 14, 4, 8)
+    bd, k_bd = _sound_speed(ph, rt, (24, 24, 24), (1, 1, 1), 24, 4, 8)
+    assert abs(k_bd / k_ax - 1) < 0.015 and abs(bd / ax - 1) <= 0.01

@@ -210,6 +210,8 @@ D3_MUTANTS = {
                                 "for (int k = 15; k < 18; ++k) rate[k] = rt.s_e;"),
     "3d entropy second moments relaxed with s_h": ("for (int k = 18; k < 21; ++k) rate[k] = rt.s_eps;",
                                                    "for (int k = 18; k < 21; ++k) rate[k] = rt.s_h;"),
+    "3d pxx_eq coefficient": ("eq[1] = 3.0 * Pi[0][0] - tr;", "eq[1] = 2.0 * Pi[0][0] - tr;"),
+    "3d pww_eq dropped": ("eq[2] = Pi[1][1] - Pi[2][2];", "eq[2] = 0.0;"),
 }
 
 
