@@ -311,3 +311,19 @@ def test_sound_speed_is_isotropic():
     dg, k_dg = _sound_speed(ph, rt, (64, 64), (1, 1), 64, 10, 30)
     assert abs(k_dg / k_ax - 1) < 0.01 and abs(dg / ax - 1) <= 0.003
     assert abs(ax / c0 - 1) <= 0.04
+
+
+def test_relaxation_spectrum_at_rest():
+    """At a uniform state at rest the one-step Jacobian is block-triangular in moment space (the
+    equilibria depend on the conserved moments only, the production vanishes): eigenvalues 1 for rho, J,
+    zeta (4) and 1 - s for each relaxed family: s_e for e, xx, xy (3), s_q for q (2), s_h for h (1),
+    s_psi (2), s_eps for eps and xi (2). Distinct rates make every assignment visible."""
+    ph = D.default_phys()
+    rt = D.rates(1.3, s_q=1.55, s_h=1.1, s_eps=0.9)
+    rt.s_psi = 0.7
+    J = _collision_jacobian(ph, rt)
+    ev = np.linalg.eigvals(J)
+    want = np.sort(np.array([1.0] * 4 + [1 - rt.s_e] * 3 + [1 - rt.s_q] * 2 + [1 - rt.s_h] +
+                            [1 - rt.s_psi] * 2 + [1 - rt.s_eps] * 2))
+    assert np.abs(ev.imag).max() <= 1e-6
+    assert np.abs(np.sort(ev.real) - want).max() <= 1e-6

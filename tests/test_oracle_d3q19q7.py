@@ -351,3 +351,20 @@ def test_sound_speed_is_isotropic():
     ax, k_ax = _sound_speed(ph, rt, (3, 3, 14), (1, 0, 0), 14, 4, 8)
     bd, k_bd = _sound_speed(ph, rt, (24, 24, 24), (1, 1, 1), 24, 4, 8)
     assert abs(k_bd / k_ax - 1) < 0.015 and abs(bd / ax - 1) <= 0.01
+
+
+def test_relaxation_spectrum_at_rest():
+    """At a uniform state at rest the equilibria depend on the conserved moments only and the production
+    vanishes, so the one-step Jacobian is block-triangular in moment space: its eigenvalues are 1 for
+    the five conserved moments and 1 - s for each relaxed family, with the family's size: s_e for e and
+    the five deviators (6), s_q for q and m (6), s_h for the fourth-order moments (3), s_psi (3) and s_eps
+    (3). Distinct rates make every assignment of a family to its rate visible."""
+    ph = D.default_phys(s0=0.05)
+    rt = D.rates(1.3, s_q=1.55, s_h=1.1, s_eps=0.9)
+    rt.s_psi = 0.7
+    J = _jacobian(ph, rt, s=0.05)
+    got = np.sort(np.linalg.eigvals(J).real)
+    want = np.sort(np.array([1.0] * 5 + [1 - rt.s_e] * 6 + [1 - rt.s_q] * 6 + [1 - rt.s_h] * 3 +
+                            [1 - rt.s_psi] * 3 + [1 - rt.s_eps] * 3))
+    assert np.abs(np.linalg.eigvals(J).imag).max() <= 1e-6
+    assert np.abs(got - want).max() <= 1e-6

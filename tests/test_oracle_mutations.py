@@ -166,6 +166,8 @@ D2_MUTANTS = {
                            "const double Exx = s * Pyy + L, Eyy = s * Pyy + L;"),
     "2d psi_y uses u_x": ("eq[7] = zeta * uy;", "eq[7] = zeta * ux;"),
     "2d M xy row": ("mm.M[6][j] = vx * vy;", "mm.M[6][j] = vx * vy * 0.5;"),
+    "2d q relaxed with s_h": ("{rt.s_e, rt.s_e, rt.s_e, rt.s_q, rt.s_q, rt.s_h,", "{rt.s_e, rt.s_e, rt.s_e, rt.s_h, rt.s_h, rt.s_h,"),
+    "2d xi relaxed with s_psi": ("rt.s_psi, rt.s_psi, rt.s_eps, rt.s_eps};", "rt.s_psi, rt.s_psi, rt.s_eps, rt.s_psi};"),
 }
 
 
@@ -212,6 +214,12 @@ D3_MUTANTS = {
                                                    "for (int k = 18; k < 21; ++k) rate[k] = rt.s_h;"),
     "3d pxx_eq coefficient": ("eq[1] = 3.0 * Pi[0][0] - tr;", "eq[1] = 2.0 * Pi[0][0] - tr;"),
     "3d pww_eq dropped": ("eq[2] = Pi[1][1] - Pi[2][2];", "eq[2] = 0.0;"),
+    "3d m_eq not zero": ("for (int a = 0; a < 3; ++a) eq[9 + a] = 0.0;", "for (int a = 0; a < 3; ++a) eq[9 + a] = 0.1 * l2 * rho * u[a];"),
+    "3d piww Q4 sign": ("+ 3.0 * (Qxy - Qxz);", "+ 3.0 * (Qxz - Qxy);"),
+    "3d eps_eq Q4 coefficient": ("+ 21.0 * (Qxy + Qyz + Qxz);", "+ 20.0 * (Qxy + Qyz + Qxz);"),
+    "3d z neighbour not wrapped": ("((z == Nz - 1 ? 0 : z + 1) * Ny + y) * Nx + x", "((z == Nz - 1 ? z : z + 1) * Ny + y) * Nx + x"),
+    "3d q relaxed with s_h": ("for (int k = 6; k < 12; ++k) rate[k] = rt.s_q;", "for (int k = 6; k < 12; ++k) rate[k] = rt.s_h;"),
+    "3d thermal gradient drops z": ("gT2 = gT2 + dT[a] * dT[a];", "gT2 = gT2 + (a < 2 ? dT[a] * dT[a] : 0.0);"),
 }
 
 
