@@ -152,67 +152,6 @@ def test_stability_region_in_flow_and_entropy():
     assert growth(_jacobian(ph, D.rates(1.2, s_h=1.5, s_eps=1.5), s=0.05)) > 1.04
 
 
-def _decay_rate(ph, rt, fd, proj, t1, t2):
-    a = D.run(ph, rt, fd, t1, NT)
-    b = D.run(ph, rt, a, t2 - t1, NT)
-    return -np.log(proj(D.moments(ph, b)) / proj(D.moments(ph, a))) / (t2 - t1)
-
-
-def test_shear_waves_decay_at_nu_over_3_along_axes_and_diagonals():
-    """Section 8 with theta_e ~ lambda^2 d J gives the viscous stress sigma_e dt theta; q_eq = -(2/3)
-    lambda^2 J makes it isotropic in three dimensions with shear viscosity nu/3 (nu of eq. nu-d1q3q3):
-    a shear wave of wave vector k decays at (nu/3)|k|^2 along an axis, a face diagonal (velocity in
-    the plane and normal to it) and the body diagonal, to within the O(k^2) dispersion."""
-    ph, s_e = D.default_phys(), 1.2
-    rt = D.rates(s_e)
-    nu = (1.0 / s_e - 0.5) * ph.lam * ph.dx
-    A = 1e-5
-    N = 32
-    k = 2 * np.pi / N
-    zz, yy, xx = np.mgrid[0:3, 0:N, 0:3].astype(float)
-    one, zero = np.ones_like(xx), np.zeros_like(xx)
-    w = np.sin(k * yy)
-    r = _decay_rate(ph, rt, D.init(ph, one, A * w, zero, zero, zero), lambda m: np.sum(m[..., 1] * w), 50, 250)
-    assert abs(r / (nu / 3 * k * k) - 1) <= 0.006
-    zz, yy, xx = np.mgrid[0:3, 0:N, 0:N].astype(float)
-    one, zero = np.ones_like(xx), np.zeros_like(xx)
-    w = np.sin(k * (xx + yy))
-    fd = D.init(ph, one, -A * w / np.sqrt(2), A * w / np.sqrt(2), zero, zero)
-    r = _decay_rate(ph, rt, fd, lambda m: np.sum((m[..., 2] - m[..., 1]) * w), 50, 250)
-    assert abs(r / (nu / 3 * 2 * k * k) - 1) <= 0.005
-    r = _decay_rate(ph, rt, D.init(ph, one, zero, zero, A * w, zero), lambda m: np.sum(m[..., 3] * w), 50, 250)
-    assert abs(r / (nu / 3 * 2 * k * k) - 1) <= 0.005
-    N = 24
-    k = 2 * np.pi / N
-    zz, yy, xx = np.mgrid[0:N, 0:N, 0:N].astype(float)
-    one, zero = np.ones_like(xx), np.zeros_like(xx)
-    w = np.sin(k * (xx + yy + zz))
-    fd = D.init(ph, one, A * w / np.sqrt(2), -A * w / np.sqrt(2), zero, zero)
-    r = _decay_rate(ph, rt, fd, lambda m: np.sum((m[..., 1] - m[..., 2]) * w), 30, 130)
-    assert abs(r / (nu / 3 * 3 * k * k) - 1) <= 0.03
-
-
-@pytest.mark.parametrize("beta", [1.5, 9.0])
-def test_entropy_mode_diffusivity(beta):
-    """An entropy mode at rest and uniform pressure diffuses at kappa/(rho0 c_p) + sigma_psi dt p0/rho0:
-    the section 8 flux kappa d log T plus the p d s term that section 8 neglects. Along z (the axis on
-    which both xi rows of the D3Q7 block carry the flux), for both couplings; a long wave (N = 192)
-    keeps the O(k^2) correction, which grows with sigma_psi, below the bound."""
-    ph, s_e = D.default_phys(beta=beta), 1.2
-    rt = D.rates(s_e, beta=beta)
-    sigma_e = 1.0 / s_e - 0.5
-    pred = sigma_e * ph.lam * ph.dx / ph.Pr + beta * ph.gamma / ph.Pr * sigma_e * (ph.dx / ph.lam) * ph.p0 / ph.rho0
-    N, B = 192, 1e-4
-    k = 2 * np.pi / N
-    zz = np.mgrid[0:N, 0:3, 0:3][0].astype(float)
-    s = B * np.sin(k * zz)
-    rho = ph.rho0 * np.exp(-s / ph.cp)  # uniform pressure
-    z = 0 * s
-    r = _decay_rate(ph, rt, D.init(ph, rho, z, z, z, s), lambda m: np.sum(m[..., 4] / m[..., 0] * np.sin(k * zz)),
-                    200, 800)
-    assert abs(r / (pred * k * k) - 1) <= 0.01, (beta, r / (k * k), pred)
-
-
 def test_transverse_wave_is_carried_by_the_mean_flow():
     """Galilean check of the nonlinear momentum flux rho u_a u_b: a transverse wave u_z = A sin(k x) in a
     uniform flow u_x = U translates at U (10 nodes in 200 steps at U = 0.05) to within 1 %."""
@@ -368,3 +307,64 @@ def test_relaxation_spectrum_at_rest():
                             [1 - rt.s_psi] * 3 + [1 - rt.s_eps] * 3))
     assert np.abs(np.linalg.eigvals(J).imag).max() <= 1e-6
     assert np.abs(got - want).max() <= 1e-6
+
+
+def _decay_rate(ph, rt, fd, proj, t1, t2):
+    a = D.run(ph, rt, fd, t1, NT)
+    b = D.run(ph, rt, a, t2 - t1, NT)
+    return -np.log(proj(D.moments(ph, b)) / proj(D.moments(ph, a))) / (t2 - t1)
+
+
+def test_shear_waves_decay_at_nu_over_3_along_axes_and_diagonals():
+    """Section 8 with theta_e ~ lambda^2 d J gives the viscous stress sigma_e dt theta; q_eq = -(2/3)
+    lambda^2 J makes it isotropic in three dimensions with shear viscosity nu/3 (nu of eq. nu-d1q3q3):
+    a shear wave of wave vector k decays at (nu/3)|k|^2 along an axis, a face diagonal (velocity in
+    the plane and normal to it) and the body diagonal, to within the O(k^2) dispersion."""
+    ph, s_e = D.default_phys(), 1.2
+    rt = D.rates(s_e)
+    nu = (1.0 / s_e - 0.5) * ph.lam * ph.dx
+    A = 1e-5
+    N = 32
+    k = 2 * np.pi / N
+    zz, yy, xx = np.mgrid[0:3, 0:N, 0:3].astype(float)
+    one, zero = np.ones_like(xx), np.zeros_like(xx)
+    w = np.sin(k * yy)
+    r = _decay_rate(ph, rt, D.init(ph, one, A * w, zero, zero, zero), lambda m: np.sum(m[..., 1] * w), 50, 250)
+    assert abs(r / (nu / 3 * k * k) - 1) <= 0.006
+    zz, yy, xx = np.mgrid[0:3, 0:N, 0:N].astype(float)
+    one, zero = np.ones_like(xx), np.zeros_like(xx)
+    w = np.sin(k * (xx + yy))
+    fd = D.init(ph, one, -A * w / np.sqrt(2), A * w / np.sqrt(2), zero, zero)
+    r = _decay_rate(ph, rt, fd, lambda m: np.sum((m[..., 2] - m[..., 1]) * w), 50, 250)
+    assert abs(r / (nu / 3 * 2 * k * k) - 1) <= 0.005
+    r = _decay_rate(ph, rt, D.init(ph, one, zero, zero, A * w, zero), lambda m: np.sum(m[..., 3] * w), 50, 250)
+    assert abs(r / (nu / 3 * 2 * k * k) - 1) <= 0.005
+    N = 24
+    k = 2 * np.pi / N
+    zz, yy, xx = np.mgrid[0:N, 0:N, 0:N].astype(float)
+    one, zero = np.ones_like(xx), np.zeros_like(xx)
+    w = np.sin(k * (xx + yy + zz))
+    fd = D.init(ph, one, A * w / np.sqrt(2), -A * w / np.sqrt(2), zero, zero)
+    r = _decay_rate(ph, rt, fd, lambda m: np.sum((m[..., 1] - m[..., 2]) * w), 30, 130)
+    assert abs(r / (nu / 3 * 3 * k * k) - 1) <= 0.03
+
+
+@pytest.mark.parametrize("beta", [1.5, 9.0])
+def test_entropy_mode_diffusivity(beta):
+    """An entropy mode at rest and uniform pressure diffuses at kappa/(rho0 c_p) + sigma_psi dt p0/rho0:
+    the section 8 flux kappa d log T plus the p d s term that section 8 neglects. Along z (the axis on
+    which both xi rows of the D3Q7 block carry the flux), for both couplings; a long wave (N = 192)
+    keeps the O(k^2) correction, which grows with sigma_psi, below the bound."""
+    ph, s_e = D.default_phys(beta=beta), 1.2
+    rt = D.rates(s_e, beta=beta)
+    sigma_e = 1.0 / s_e - 0.5
+    pred = sigma_e * ph.lam * ph.dx / ph.Pr + beta * ph.gamma / ph.Pr * sigma_e * (ph.dx / ph.lam) * ph.p0 / ph.rho0
+    N, B = 192, 1e-4
+    k = 2 * np.pi / N
+    zz = np.mgrid[0:N, 0:3, 0:3][0].astype(float)
+    s = B * np.sin(k * zz)
+    rho = ph.rho0 * np.exp(-s / ph.cp)  # uniform pressure
+    z = 0 * s
+    r = _decay_rate(ph, rt, D.init(ph, rho, z, z, z, s), lambda m: np.sum(m[..., 4] / m[..., 0] * np.sin(k * zz)),
+                    200, 800)
+    assert abs(r / (pred * k * k) - 1) <= 0.01, (beta, r / (k * k), pred)
