@@ -85,13 +85,44 @@ __host__ __device__ P3T<R> lanes3(const P3& p) {
 
 // The logarithm and exponential of the one-dimensional kernels (lbm_internal.cuh): FP32 CUDA's
 // log1pf / expm1f, FP64 the double-float series on the FP32 pipes. Reciprocals: FP32 a division,
-// FP64 an FP32 estimate refined by two FP64 Newton steps.
-__device__ __forceinline__ float rcp3(float x) { return 1.0f / x; }
-__device__ __forceinline__ double rcp3(double x) { return lbm::m_rcp(x); }
-__device__ __forceinline__ float lg3(float x) { return lbm::m_log1p(x); }
-__device__ __forceinline__ double lg3(double x) { return lbm::m_log1p(x); }
-__device__ __forceinline__ float ex3(float x) { return lbm::m_expm1(x); }
-__device__ __forceinline__ double ex3(double x) { return lbm::m_expm1(x); }
+// FP64 an FP32 estimate refined by two FP64 Newton steps. A host build (the node update emulated on the
+// CPU by the tests) takes the C library's log1p, expm1 and a division instead.
+__host__ __device__ __forceinline__ float rcp3(float x) { return 1.0f / x; }
+__host__ __device__ __forceinline__ double rcp3(double x) {
+#ifdef __CUDA_ARCH__
+  return lbm::m_rcp(x);
+#else
+  return 1.0 / x;
+#endif
+}
+__host__ __device__ __forceinline__ float lg3(float x) {
+#ifdef __CUDA_ARCH__
+  return lbm::m_log1p(x);
+#else
+  return std::log1p(x);
+#endif
+}
+__host__ __device__ __forceinline__ double lg3(double x) {
+#ifdef __CUDA_ARCH__
+  return lbm::m_log1p(x);
+#else
+  return std::log1p(x);
+#endif
+}
+__host__ __device__ __forceinline__ float ex3(float x) {
+#ifdef __CUDA_ARCH__
+  return lbm::m_expm1(x);
+#else
+  return std::expm1(x);
+#endif
+}
+__host__ __device__ __forceinline__ double ex3(double x) {
+#ifdef __CUDA_ARCH__
+  return lbm::m_expm1(x);
+#else
+  return std::expm1(x);
+#endif
+}
 // LBM_F64_DF: FP64 planes, the node update in double-float (lbm_dfn.cuh).
 using lbm::dfn;
 __device__ __forceinline__ dfn rcp3(dfn x) { return lbm::dfn_rcp(x); }
@@ -152,7 +183,7 @@ struct Thermo3 {
 };
 
 template <typename R>
-__device__ __forceinline__ Thermo3<R> thermo3(const Cons3<R>& c, const P3T<R>& p) {
+__host__ __device__ __forceinline__ Thermo3<R> thermo3(const Cons3<R>& c, const P3T<R>& p) {
   Thermo3<R> t;
   t.inv = rcp3(R(1) + c.r);
   t.ux = c.jx * t.inv;
@@ -316,8 +347,8 @@ __host__ __device__ __forceinline__ long long wrap3(long long v, long long n) {
 // One node's collision: relaxation of the 21 non-conserved moments and the production added to
 // zeta; du[a][b] and dT[a] are the centred differences (without the 1/2) along axis a of u_b and T'.
 template <typename R>
-__device__ __forceinline__ void collide3(R (&f)[kQ], const P3T<R>& p, const R (&du)[3][3], const R (&dT)[3],
-                                         R Tn) {
+__host__ __device__ __forceinline__ void collide3(R (&f)[kQ], const P3T<R>& p, const R (&du)[3][3], const R (&dT)[3],
+                                                     R Tn) {
   Cons3<R> c = conserved3(f);
   const Thermo3<R> t = thermo3(c, p);
   R m[21], eq[21];
